@@ -1,0 +1,136 @@
+/*
+ * hexval.h -- C ABI of the GB300 (sm_103a) validity test of linear hexahedra.
+ *
+ * Method: Johnen, Weill & Remacle, "Robust and efficient validation of the
+ * linear hexahedral element", IMR 2017.  For every hexahedron the library
+ * evaluates the Jacobian determinant J at the 8 corners and 12 edge midpoints
+ * (Sec. 5: triple products of edge vectors), maps them to the 27 Bezier
+ * coefficients of the triquadratic J (Sec. 4, Table t:Tsmall), and classifies
+ * the element (Sec. 6): a non-positive sample -> invalid; 27 positive
+ * coefficients -> valid; otherwise the coefficients are refined by Bezier
+ * subdivision (Sec. 3.1, Sec. 6) until the element is decided or the depth
+ * cap is reached.
+ *
+ * Exactness: every sign decision is certified with a forward-error bound; a
+ * decision the bound cannot settle is redone in higher precision (FP32 ->
+ * FP64) and finally in exact integer arithmetic on the device, so the
+ * verdicts are those of exact arithmetic on the FP64 inputs.
+ *
+ * Conventions shared by every entry point:
+ *  - array arguments are DEVICE pointers owned by the caller (unless a name
+ *    says _host); the library never frees them and never keeps them after
+ *    the call has been enqueued;
+ *  - calls are stream ordered and enqueue only: no host synchronisation and
+ *    no allocation (all scratch is owned by the handle, allocated in
+ *    hexval_create); results are visible once the stream reaches them;
+ *  - one handle must not be used by two streams at the same time (its
+ *    scratch is shared by the calls made on it);
+ *  - host-detectable errors return a negative code and enqueue nothing;
+ *    device-detected errors (bad connectivity, exhausted work queue, range of
+ *    the exact tier) never trap: they set a sticky status read back by
+ *    hexval_status, and the affected elements get verdict UNDECIDED.
+ */
+#ifndef HEXVAL_H
+#define HEXVAL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hexval_ctx* hexval_handle;
+
+/* return / status codes */
+enum {
+  HEXVAL_OK = 0,
+  HEXVAL_E_ARG = -1,     /* bad argument (null pointer, negative size, ...) */
+  HEXVAL_E_NOMEM = -2,   /* device allocation failed in hexval_create */
+  HEXVAL_E_CUDA = -3,    /* a CUDA runtime call failed */
+  HEXVAL_E_INDEX = -4,   /* device: connectivity entry outside [0, n_nodes) */
+  HEXVAL_E_QUEUE = -5,   /* device: refinement queue or escalation list full */
+  HEXVAL_E_TIMEOUT = -6, /* device: a bounded wait gave up */
+  HEXVAL_E_RANGE = -7    /* device: element outside the exact tier's range */
+};
+
+/* precision of the bulk pass */
+enum { HEXVAL_FP64 = 0, HEXVAL_FP32_FILTERED = 1 };
+
+/* verdict in bits 0-2 of a flag byte; bits 3-6 hold the decision depth,
+ * bit 7 marks an element that needed the exact tier (diagnostic only) */
+enum {
+  HEXVAL_VALID = 1,     /* J > 0 on the whole element */
+  HEXVAL_INVALID = 2,   /* J <= 0 somewhere */
+  HEXVAL_UNDECIDED = 3, /* depth cap reached, or a device error (see status) */
+  HEXVAL_NONFINITE = 4  /* a coordinate is NaN or infinite */
+};
+
+typedef struct {
+  uint32_t struct_size;    /* sizeof(hexval_config): ABI versioning */
+  int32_t device;          /* CUDA device ordinal */
+  int32_t precision;       /* HEXVAL_FP64 or HEXVAL_FP32_FILTERED */
+  int32_t max_depth;       /* refinement cap D, 0..15 (default 8) */
+  uint64_t max_batch;      /* elements per internal batch (default 2^24) */
+  uint64_t queue_capacity; /* boxes per refinement level (default 2^23) */
+  uint64_t max_nodes;      /* node capacity of the FP32 indexed path (default 2^24) */
+  uint64_t exact_capacity; /* elements per batch for the exact tier (default 2^16) */
+} hexval_config;
+
+typedef struct {
+  uint64_t elements;        /* elements processed since the last reset */
+  uint64_t escalated_fp64;  /* FP32 decisions redone in FP64 */
+  uint64_t refined;         /* elements that needed subdivision */
+  uint64_t boxes;           /* boxes examined by the refinement */
+  uint64_t exact;           /* elements decided by the exact tier */
+  uint64_t max_level_boxes; /* largest refinement level (boxes) */
+} hexval_stats;
+
+/* Fills *cfg with the defaults listed above. */
+int hexval_config_default(hexval_config* cfg);
+
+/* Creates a handle on cfg->device and allocates all of its device scratch
+ * (about 460 B x queue_capacity + 24 B x max_nodes + 9 B x max_batch with
+ * the defaults: ~4.4 GB).  Returns HEXVAL_E_NOMEM if that fails. */
+int hexval_create(const hexval_config* cfg, hexval_handle* out);
+
+/* Frees the handle's scratch (synchronises its device). */
+int hexval_destroy(hexval_handle h);
+
+/* Independent elements.
+ *   corners: FP64, n_hex*24 values laid out as 24 planes [8][3][n_hex]: value
+ *            (k, d, e) at corners[(3*k + d)*n_hex + e] is coordinate d (x,y,z)
+ *            of node k (node order of Appendix A) of element e;
+ *   flags:   n_hex bytes (verdict | depth << 3 | exact << 7);
+ *   bmin, bmax: n_hex FP64 each, the min / max of the element's 27 depth-0
+ *            Bezier coefficients (FP32-accurate for elements the FP32 bulk
+ *            pass decided); either may be NULL;
+ *   stream:  a cudaStream_t (NULL = legacy default stream).
+ * n_hex may be 0 (nothing is enqueued) and must be < 2^31. */
+int hexval_check_soa(hexval_handle h, int64_t n_hex, const double* corners, uint8_t* flags,
+                     double* bmin, double* bmax, void* stream);
+
+/* Elements of an indexed mesh.
+ *   nodes: FP64 [n_nodes][3] (x, y, z of each node);
+ *   conn:  int32 [n_hex][8], 0-based node ids in Appendix A order.
+ * An entry outside [0, n_nodes) gives that element verdict UNDECIDED and the
+ * sticky status HEXVAL_E_INDEX.  Other arguments as hexval_check_soa.  With
+ * HEXVAL_FP32_FILTERED, n_nodes must not exceed the handle's max_nodes. */
+int hexval_check_indexed(hexval_handle h, int64_t n_nodes, const double* nodes, int64_t n_hex,
+                         const int32_t* conn, uint8_t* flags, double* bmin, double* bmax,
+                         void* stream);
+
+/* Synchronises the stream, returns the sticky device status (HEXVAL_OK or
+ * the most severe device-detected code) and clears it. */
+int hexval_status(hexval_handle h, void* stream);
+
+/* Synchronises the stream and copies the counters; reset != 0 zeroes them. */
+int hexval_get_stats(hexval_handle h, hexval_stats* out, int reset, void* stream);
+
+/* Static description of a code. */
+const char* hexval_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEXVAL_H */

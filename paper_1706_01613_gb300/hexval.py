@@ -1,0 +1,230 @@
+"""Thin ctypes binding of libhexval (C ABI in include/hexval.h).
+
+Argument marshalling only: every step of the validity test runs in the CUDA
+kernels of the library.  PyTorch provides device memory and streams.  There is
+no CPU fallback: if the library is missing or no GPU is present, the calls
+raise.
+
+    v = Validator(precision="fp32")          # or "fp64"
+    flags, bmin, bmax = v.check_soa(corners)  # corners: (8, 3, n) float64 CUDA
+    flags, bmin, bmax = v.check_indexed(nodes, conn)
+    v.raise_on_status()                       # sticky device-side errors
+"""
+import ctypes
+import os
+
+from . import _build
+
+HEXVAL_OK = 0
+CODES = {0: "HEXVAL_OK", -1: "HEXVAL_E_ARG", -2: "HEXVAL_E_NOMEM", -3: "HEXVAL_E_CUDA",
+         -4: "HEXVAL_E_INDEX", -5: "HEXVAL_E_QUEUE", -6: "HEXVAL_E_TIMEOUT",
+         -7: "HEXVAL_E_RANGE"}
+FP64, FP32_FILTERED = 0, 1
+VALID, INVALID, UNDECIDED, NONFINITE = 1, 2, 3, 4
+
+# every function declared in include/hexval.h (the CPU test checks the list)
+EXPORTS = ("hexval_config_default", "hexval_create", "hexval_destroy", "hexval_check_soa",
+           "hexval_check_indexed", "hexval_status", "hexval_get_stats", "hexval_strerror")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("device", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("max_depth", ctypes.c_int32),
+                ("max_batch", ctypes.c_uint64), ("queue_capacity", ctypes.c_uint64),
+                ("max_nodes", ctypes.c_uint64), ("exact_capacity", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in
+                ("elements", "escalated_fp64", "refined", "boxes", "exact", "max_level_boxes")]
+
+
+class HexvalError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s%s (%d: %s)" % (what + ": " if what else "", CODES.get(code, "?"),
+                                            code, strerror(code)))
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Loads libhexval.so (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError("libhexval.so is not built (%s); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    lib.hexval_config_default.argtypes = [ctypes.POINTER(Config)]
+    lib.hexval_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(vp)]
+    lib.hexval_destroy.argtypes = [vp]
+    lib.hexval_check_soa.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    lib.hexval_check_indexed.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, vp]
+    lib.hexval_status.argtypes = [vp, vp]
+    lib.hexval_get_stats.argtypes = [vp, ctypes.POINTER(Stats), ctypes.c_int, vp]
+    lib.hexval_strerror.argtypes = [ctypes.c_int]
+    lib.hexval_strerror.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def strerror(code):
+    try:
+        return load().hexval_strerror(int(code)).decode()
+    except Exception:  # library not loadable: fall back to the code name
+        return CODES.get(code, "?")
+
+
+def default_config():
+    cfg = Config()
+    rc = load().hexval_config_default(ctypes.byref(cfg))
+    if rc != HEXVAL_OK:
+        raise HexvalError(rc, "hexval_config_default")
+    return cfg
+
+
+def _check(rc, what):
+    if rc != HEXVAL_OK:
+        raise HexvalError(rc, what)
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Validator:
+    """One library handle (its device scratch is allocated here).
+
+    precision: "fp64" (plain FP64 bulk pass) or "fp32" (FP32-filtered bulk
+    pass with certified escalation).  The remaining keywords override fields
+    of the default configuration (max_depth, queue_capacity, max_batch,
+    max_nodes, exact_capacity)."""
+
+    def __init__(self, precision="fp64", max_depth=8, device=None, **caps):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("hexval needs a CUDA device")
+        lib = load()
+        cfg = default_config()
+        cfg.device = torch.cuda.current_device() if device is None else int(device)
+        cfg.precision = {"fp64": FP64, "fp32": FP32_FILTERED}[precision]
+        cfg.max_depth = int(max_depth)
+        for k, v in caps.items():
+            setattr(cfg, k, int(v))
+        self.config = cfg
+        self.precision = precision
+        self.device = torch.device("cuda", cfg.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib.hexval_create(ctypes.byref(cfg), ctypes.byref(h)), "hexval_create")
+        self._h = h
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hexval_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ calls ----
+    def _outputs(self, n, out):
+        import torch
+        if out is not None:
+            return out
+        return (torch.empty(n, dtype=torch.uint8, device=self.device),
+                torch.empty(n, dtype=torch.float64, device=self.device),
+                torch.empty(n, dtype=torch.float64, device=self.device))
+
+    @staticmethod
+    def _ptr(t):
+        return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p()
+
+    def check_soa(self, corners, out=None, stream=None):
+        """corners: contiguous float64 CUDA tensor (8, 3, n).  Returns
+        (flags uint8, bmin float64, bmax float64), enqueued on `stream`
+        (default: the current stream).  `out` = preallocated triple (bmin
+        and bmax may be None)."""
+        import torch
+        if corners.dtype != torch.float64 or not corners.is_cuda or not corners.is_contiguous():
+            raise ValueError("corners must be a contiguous float64 CUDA tensor (8, 3, n)")
+        if corners.dim() != 3 or tuple(corners.shape[:2]) != (8, 3):
+            raise ValueError("corners must have shape (8, 3, n)")
+        n = corners.shape[2]
+        flags, bmin, bmax = self._outputs(n, out)
+        rc = self._lib.hexval_check_soa(self._h, n, self._ptr(corners), self._ptr(flags),
+                                        self._ptr(bmin), self._ptr(bmax), _stream_ptr(stream))
+        _check(rc, "hexval_check_soa")
+        return flags, bmin, bmax
+
+    def check_indexed(self, nodes, conn, out=None, stream=None):
+        """nodes: float64 CUDA (n_nodes, 3); conn: int32 CUDA (n_hex, 8)."""
+        import torch
+        if nodes.dtype != torch.float64 or not nodes.is_cuda or not nodes.is_contiguous():
+            raise ValueError("nodes must be a contiguous float64 CUDA tensor (n_nodes, 3)")
+        if conn.dtype != torch.int32 or not conn.is_cuda or not conn.is_contiguous():
+            raise ValueError("conn must be a contiguous int32 CUDA tensor (n_hex, 8)")
+        if nodes.dim() != 2 or nodes.shape[1] != 3 or conn.dim() != 2 or conn.shape[1] != 8:
+            raise ValueError("bad shapes")
+        n = conn.shape[0]
+        flags, bmin, bmax = self._outputs(n, out)
+        rc = self._lib.hexval_check_indexed(self._h, nodes.shape[0], self._ptr(nodes), n,
+                                            self._ptr(conn), self._ptr(flags), self._ptr(bmin),
+                                            self._ptr(bmax), _stream_ptr(stream))
+        _check(rc, "hexval_check_indexed")
+        return flags, bmin, bmax
+
+    def check_host(self, kind, *arrays, stream=None):
+        """End-to-end call on host data: copies the inputs (pinned host
+        tensors) to the device, runs the check and copies the flags back.
+        kind = "soa" (corners) or "indexed" (nodes, conn).  Returns the host
+        flags tensor (uint8)."""
+        dev = [a.to(self.device, non_blocking=True) for a in arrays]
+        if kind == "soa":
+            flags, _, _ = self.check_soa(dev[0], out=self._outputs(dev[0].shape[2], None)[:1]
+                                         + (None, None), stream=stream)
+        else:
+            flags, _, _ = self.check_indexed(dev[0], dev[1],
+                                             out=self._outputs(dev[1].shape[0], None)[:1]
+                                             + (None, None), stream=stream)
+        return flags.to("cpu")
+
+    def status(self, stream=None):
+        """Synchronises and returns (and clears) the sticky device status."""
+        return self._lib.hexval_status(self._h, _stream_ptr(stream))
+
+    def raise_on_status(self, stream=None):
+        rc = self.status(stream)
+        if rc != HEXVAL_OK:
+            raise HexvalError(rc, "device status")
+
+    def stats(self, reset=False, stream=None):
+        s = Stats()
+        _check(self._lib.hexval_get_stats(self._h, ctypes.byref(s), int(reset),
+                                          _stream_ptr(stream)), "hexval_get_stats")
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+def verdict(flags):
+    return flags & 7
+
+
+def depth(flags):
+    return (flags >> 3) & 15

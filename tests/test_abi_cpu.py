@@ -1,0 +1,69 @@
+"""The C-ABI library builds, loads without a GPU and exports every function
+that include/hexval.h declares; host-side argument checks need no device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1706_01613_gb300 import _build
+from paper_1706_01613_gb300 import hexval as hv
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "hexval.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hexval_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return hv.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 8
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(hv.EXPORTS) == names
+
+
+def test_default_config(lib):
+    cfg = hv.default_config()
+    assert cfg.struct_size == ctypes.sizeof(hv.Config)
+    assert (cfg.precision, cfg.max_depth) == (hv.FP64, 8)
+    assert cfg.max_batch == 1 << 24 and cfg.queue_capacity == 1 << 23
+    assert cfg.exact_capacity == 1 << 16 and cfg.max_nodes == 1 << 24
+
+
+def test_host_side_argument_errors(lib):
+    null = ctypes.c_void_p()
+    assert lib.hexval_check_soa(null, 10, null, null, null, null, null) == -1
+    assert lib.hexval_check_indexed(null, 1, null, 1, null, null, null, null, null) == -1
+    assert lib.hexval_status(null, null) == -1
+    assert lib.hexval_destroy(null) == -1
+    assert lib.hexval_create(None, ctypes.byref(ctypes.c_void_p())) == -1
+    bad = hv.default_config()
+    bad.max_depth = 16
+    assert lib.hexval_create(ctypes.byref(bad), ctypes.byref(ctypes.c_void_p())) == -1
+    bad = hv.default_config()
+    bad.struct_size = 3
+    assert lib.hexval_create(ctypes.byref(bad), ctypes.byref(ctypes.c_void_p())) == -1
+
+
+def test_strerror(lib):
+    for code, name in hv.CODES.items():
+        assert lib.hexval_strerror(code).decode()
+    assert lib.hexval_strerror(-99).decode() == "unknown code"
+
+
+def test_binding_refuses_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError):
+        hv.Validator()

@@ -1,0 +1,287 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Flags (verdict and decision depth) must be bit-identical; bit 7 (exact tier
+used) is diagnostic and masked.  bmin/bmax: the FP64 form within 1e-12 of the
+oracle relative to max |coefficient|; the FP32-decided elements within their
+certified FP32 bound, checked here against 2e-3 relative (the bound's worst
+case for these inputs), and the observed error is printed.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1706_01613_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # collected on CPU hosts, skipped there
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1706_01613_gb300 import hexval as hv  # noqa: E402
+
+from . import test_oracle_pins as pins  # noqa: E402
+
+TOL64 = 1e-12
+TOL32 = 2e-3
+CAPS = dict(queue_capacity=1 << 21, max_batch=1 << 22, max_nodes=1 << 22, exact_capacity=1 << 14)
+
+
+@pytest.fixture(scope="module")
+def validators():
+    vs = {}
+    for prec in ("fp64", "fp32"):
+        for d in (8, 12):
+            vs[(prec, d)] = hv.Validator(precision=prec, max_depth=d, **CAPS)
+    yield vs
+    for v in vs.values():
+        v.close()
+
+
+def _run_soa(v, X):
+    f, lo, hi = v.check_soa(torch.from_numpy(np.ascontiguousarray(X)).cuda())
+    rc = v.status()
+    return f.cpu().numpy(), lo.cpu().numpy(), hi.cpu().numpy(), rc
+
+
+def _compare(prec, got, want, tol32=TOL32):
+    f, lo, hi = got
+    wf, wlo, whi = want
+    bad = np.nonzero((f & 0x7F) != (wf & 0x7F))[0]
+    assert len(bad) == 0, "flags differ at %s: got %s want %s" % (
+        bad[:10], f[bad[:10]] & 0x7F, wf[bad[:10]] & 0x7F)
+    fin = np.isfinite(wlo)
+    scale = np.maximum(np.abs(wlo), np.abs(whi))[fin]
+    err = np.maximum(np.abs(lo[fin] - wlo[fin]), np.abs(hi[fin] - whi[fin]))
+    rel = err / np.where(scale > 0, scale, 1.0)
+    tol = TOL64 if prec == "fp64" else tol32
+    assert np.all(rel <= tol), "coefficient error %g > %g" % (rel.max(), tol)
+    assert np.array_equal(np.isnan(lo), np.isnan(wlo))
+    return float(rel.max()) if len(rel) else 0.0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_paper_worked_examples(validators, prec):
+    X = np.stack([np.array(e["nodes"], float) for e in pins._examples()], axis=2)
+    got = _run_soa(validators[(prec, 8)], X)
+    assert got[3] == 0
+    _compare(prec, got[:3], oracle.check_soa(X, max_depth=8))
+    assert [int(x) & 0x7F for x in got[0]] == [2 | 3 << 3, 1 | 1 << 3, 2]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_perturbed_cubes_10000(validators, prec):
+    """10,000 unit cubes with U[-0.3, 0.3] corner noise (seed 20170001)."""
+    X = synth.perturbed_cubes(10_000)
+    got = _run_soa(validators[(prec, 8)], X)
+    rel = _compare(prec, got[:3], oracle.check_soa(X, max_depth=8))
+    print("%s max rel coefficient error %.3g" % (prec, rel))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 255, 257, 1000, 4097])
+def test_ragged_sizes(validators, prec, n):
+    X = synth.perturbed_cubes(n, noise=0.5, seed=1000 + n)
+    got = _run_soa(validators[(prec, 8)], X)
+    _compare(prec, got[:3], oracle.check_soa(X, max_depth=8))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_refinement_heavy(validators, prec):
+    """Prisms twisted by up to 180 degrees with aspect ratios up to 1000:
+    decisions up to depth 11 (depth cap 12)."""
+    X = synth.twisted_layers(20_000, seed=4444, theta_max_deg=180.0)
+    v = validators[(prec, 12)]
+    v.stats(reset=True)
+    got = _run_soa(v, X)
+    want = oracle.check_soa(X, max_depth=12)
+    _compare(prec, got[:3], want)
+    assert (want[0] >> 3 & 15).max() >= 6
+    st = v.stats()
+    assert st["refined"] > 1000 and st["boxes"] > 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_depth_caps(prec):
+    X = synth.twisted_layers(5000, seed=4545, theta_max_deg=180.0)
+    for d in (0, 1, 2, 5):
+        v = hv.Validator(precision=prec, max_depth=d, **CAPS)
+        got = _run_soa(v, X)
+        _compare(prec, got[:3], oracle.check_soa(X, max_depth=d))
+        v.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_degenerate_go_exact(validators, prec):
+    """Exact zeros: collapsed edge, flat element, 180-degree twist, and 200
+    elements whose corner-1 J is exactly 0 but rounds to noise of either sign."""
+    ref = synth.REF_CORNERS
+    X1 = ref.copy()
+    X1[1] = X1[0]
+    X2 = ref.copy()
+    X2[:, 2] = 0.0
+    X = np.concatenate([np.stack([X1, X2, pins.TWIST180], axis=2),
+                        pins._zero_corner_elements(200, 19)], axis=2)
+    got = _run_soa(validators[(prec, 8)], X)
+    want = oracle.check_soa(X, max_depth=8)
+    _compare(prec, got[:3], want)
+    assert np.all(got[0] & 0x7F == 2)
+    assert np.all(got[0] & 0x80)  # decided by the exact tier
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_nonfinite_and_empty(validators, prec):
+    v = validators[(prec, 8)]
+    X = np.stack([synth.REF_CORNERS.copy() for _ in range(3)], axis=2)
+    X[2, 1, 0] = np.nan
+    X[5, 0, 1] = np.inf
+    f, lo, hi, rc = _run_soa(v, X)
+    assert rc == 0 and list(f & 7) == [4, 4, 1] and np.isnan(lo[0]) and lo[2] == 1.0
+    f, _, _ = v.check_soa(torch.zeros((8, 3, 0), dtype=torch.float64, device="cuda"))
+    assert f.numel() == 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_indexed_small_grid(validators, prec):
+    nodes, conn = synth.structured_grid(24, 20, 16, sigma=0.3, seed=31)
+    v = validators[(prec, 8)]
+    f, lo, hi = v.check_indexed(torch.from_numpy(nodes).cuda(), torch.from_numpy(conn).cuda())
+    assert v.status() == 0
+    want = oracle.check_indexed(nodes, conn, max_depth=8)
+    _compare(prec, (f.cpu().numpy(), lo.cpu().numpy(), hi.cpu().numpy()), want)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_bad_connectivity_sets_status(validators, prec):
+    nodes, conn = synth.structured_grid(6, 5, 4, sigma=0.2, seed=5)
+    conn = conn.copy()
+    conn[7, 3] = nodes.shape[0]
+    conn[9, 0] = -1
+    v = validators[(prec, 8)]
+    f, lo, _ = v.check_indexed(torch.from_numpy(nodes).cuda(), torch.from_numpy(conn).cuda())
+    assert v.status() == -4  # HEXVAL_E_INDEX
+    f = f.cpu().numpy()
+    assert f[7] & 7 == 3 and f[9] & 7 == 3 and np.isnan(lo.cpu().numpy()[7])
+    ok = np.ones(len(conn), bool)
+    ok[[7, 9]] = False
+    good_conn = conn.copy()
+    good_conn[7] = conn[8]
+    good_conn[9] = conn[8]
+    want = oracle.check_indexed(nodes, good_conn, max_depth=8)[0]
+    assert np.array_equal(f[ok] & 0x7F, want[ok] & 0x7F)
+    assert v.status() == 0  # the status is cleared once read
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tiny_queue_overflows_into_exact_tier(prec):
+    """With a refinement queue of 16 boxes the overflowing elements are
+    decided by the exact tier: the flags stay exact and the status says so."""
+    X = synth.twisted_layers(3000, seed=4646, theta_max_deg=180.0)
+    v = hv.Validator(precision=prec, max_depth=10, queue_capacity=16, max_batch=1 << 16,
+                     max_nodes=1 << 10, exact_capacity=1 << 14)
+    got = _run_soa(v, X)
+    assert got[3] == -5
+    _compare(prec, got[:3], oracle.check_soa(X, max_depth=10))
+    v.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batching_is_invisible(prec):
+    X = synth.perturbed_cubes(10_000, noise=0.5, seed=99)
+    a = hv.Validator(precision=prec, max_depth=8, **CAPS)
+    b = hv.Validator(precision=prec, max_depth=8, queue_capacity=1 << 16, max_batch=777,
+                     max_nodes=1 << 10, exact_capacity=1 << 10)
+    ga, gb = _run_soa(a, X), _run_soa(b, X)
+    for x, y in zip(ga[:3], gb[:3]):
+        assert np.array_equal(x, y, equal_nan=True)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_affine_mixture_escalation(validators, prec):
+    """Precision-stress mixture: 5% near-degenerate elements (|min J/max J|
+    <= 1e-6) must be escalated by the FP32 form and still get exact flags."""
+    X, kind, r = synth.affine_mixture(200_000, seed=20170003)
+    v = validators[(prec, 8)]
+    v.stats(reset=True)
+    got = _run_soa(v, X)
+    rel = _compare(prec, got[:3], oracle.check_soa(X, max_depth=8))
+    st = v.stats()
+    print("%s: %s max rel coefficient error %.3g" % (prec, st, rel))
+    if prec == "fp32":
+        assert st["escalated_fp64"] >= (kind == 1).sum()
+
+
+def test_cuda_graph_capture_replays():
+    X = torch.from_numpy(synth.perturbed_cubes(5000, noise=0.5, seed=3)).cuda()
+    v = hv.Validator(precision="fp32", max_depth=8, **CAPS)
+    out = (torch.empty(5000, dtype=torch.uint8, device="cuda"),
+           torch.empty(5000, dtype=torch.float64, device="cuda"),
+           torch.empty(5000, dtype=torch.float64, device="cuda"))
+    ref = [t.clone() for t in v.check_soa(X)]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        v.check_soa(X, out=out, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        v.check_soa(X, out=out)
+    for t in out:
+        t.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(out, ref):
+        assert torch.equal(a, b)
+    v.close()
+
+
+# ------------------------------------------- full-size inputs, sampled ----
+
+def _sample(n, k, seed):
+    return np.sort(np.random.default_rng(seed).choice(n, size=min(k, n), replace=False))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_structured_mesh_128_cubed_sampled(prec):
+    """The 128^3 indexed mesh (2,097,152 elements) in the benchmark's launch
+    configuration; 20,000 sampled elements against the oracle."""
+    nodes, conn = synth.structured_grid(128)
+    v = hv.Validator(precision=prec, max_depth=8)
+    f, lo, hi = v.check_indexed(torch.from_numpy(nodes).cuda(), torch.from_numpy(conn).cuda())
+    assert v.status() == 0
+    idx = _sample(len(conn), 20_000, 1)
+    want = oracle.check_indexed(nodes, conn[idx], max_depth=8)
+    got = (f.cpu().numpy()[idx], lo.cpu().numpy()[idx], hi.cpu().numpy()[idx])
+    _compare(prec, got, want)
+    v.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_twisted_layers_sampled(prec):
+    """4,194,304 boundary-layer elements (depth cap 10); 20,000 sampled."""
+    X = synth.twisted_layers(4_194_304)
+    v = hv.Validator(precision=prec, max_depth=10)
+    f, lo, hi = v.check_soa(torch.from_numpy(X).cuda())
+    assert v.status() == 0
+    idx = _sample(X.shape[2], 20_000, 2)
+    want = oracle.check_soa(np.ascontiguousarray(X[:, :, idx]), max_depth=10)
+    got = (f.cpu().numpy()[idx], lo.cpu().numpy()[idx], hi.cpu().numpy()[idx])
+    _compare(prec, got, want)
+    v.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_affine_mixture_sampled(prec):
+    """16,777,216 precision-stress elements; 20,000 sampled plus every
+    near-degenerate element among the first 2,000,000."""
+    X, kind, _ = synth.affine_mixture(16_777_216)
+    v = hv.Validator(precision=prec, max_depth=8)
+    f, lo, hi = v.check_soa(torch.from_numpy(X).cuda())
+    assert v.status() == 0
+    idx = np.union1d(_sample(X.shape[2], 20_000, 3), np.nonzero(kind[:2_000_000] == 1)[0][:20_000])
+    want = oracle.check_soa(np.ascontiguousarray(X[:, :, idx]), max_depth=8)
+    got = (f.cpu().numpy()[idx], lo.cpu().numpy()[idx], hi.cpu().numpy()[idx])
+    _compare(prec, got, want)
+    v.close()
