@@ -1,0 +1,457 @@
+"""Benchmark of the GB300 linear-hexahedron validity test.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config 2|1|3|4]
+
+A step is one pass of the whole hot path (bulk pass, refinement, exact tier)
+over one synthetic workload already resident in HBM.  The default workload
+is the indexed structured mesh of 128^3 hexahedra (129^3 FP64 nodes, interior
+nodes displaced by N(0, 0.15^2), int32 connectivity).  `value` is the
+FP32-filtered form; the plain FP64 form is measured on the same input and
+reported under "fp64".  Flags are exact (certified) in both forms.
+
+Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
+launch stream; L2 is flushed (256 MB write) between steps because the
+workload (119 MB) fits in the 129 MB L2.  Multi-GPU (torchrun): every rank
+validates its own mesh (weak scaling, no collective on the data path);
+barrier + synchronize around the timed region and the max over ranks.
+
+One JSON line is printed by rank 0.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "validated hexes/s on 1 GB300, FP32-filtered vs plain FP64 (exact flags); p50/p99 latency"
+UNIT = "hex/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+# ------------------------------------------------------------- workloads ----
+
+def workload(cfg, rank):
+    """Host arrays of one configuration (rank-dependent seed for replicas)."""
+    from paper_1706_01613_gb300 import synth
+    if cfg == 2:
+        nodes, conn = synth.structured_grid(128, seed=20170002 + 1000 * rank)
+        return dict(kind="indexed", nodes=nodes, conn=conn, n=conn.shape[0], depth=8,
+                    name="structured mesh 128^3 hexes (129^3 FP64 nodes, sigma 0.15, int32 conn)",
+                    bytes_per_hex=32 + 17, node_bytes=24 * nodes.shape[0])
+    if cfg == 1:
+        X = synth.perturbed_cubes(10_000, seed=20170001 + 1000 * rank)
+        return dict(kind="soa", X=X, n=X.shape[2], depth=8,
+                    name="10,000 perturbed unit cubes (U[-0.3,0.3], SoA FP64)",
+                    bytes_per_hex=192 + 17, node_bytes=0)
+    if cfg == 3:
+        X, _, _ = synth.affine_mixture(16_777_216, seed=20170003 + 1000 * rank)
+        return dict(kind="soa", X=X, n=X.shape[2], depth=8,
+                    name="16,777,216 affine / near-degenerate / inverted hexes (SoA FP64)",
+                    bytes_per_hex=192 + 17, node_bytes=0)
+    if cfg == 4:
+        X = synth.twisted_layers(4_194_304, seed=20170004 + 1000 * rank)
+        return dict(kind="soa", X=X, n=X.shape[2], depth=10,
+                    name="4,194,304 twisted boundary-layer hexes (SoA FP64, depth cap 10)",
+                    bytes_per_hex=192 + 17, node_bytes=0)
+    raise ValueError(cfg)
+
+
+def algorithmic_bytes(w):
+    return w["bytes_per_hex"] * w["n"] + w["node_bytes"]
+
+
+# ------------------------------------------------------------ clock probe ---
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, max clock, throttle reasons) while the
+    timed region runs."""
+    FIELDS = ("pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id):
+        self.bus_id = (bus_id or "").lower()
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [r for t, r in self.rows if len(r) >= 9 and
+                (not self.bus_id or self.bus_id.endswith(r[0].lower()[-12:]))]
+        inside = [r for t, r in self.rows if t0 <= t <= t1 and len(r) >= 9]
+        use = inside if inside else rows
+        if not use:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = sorted(float(r[1]) for r in use if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in use if r[2].replace(".", "").isdigit())
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in use:
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(use),
+                "window": "timed region" if inside else "whole run (timed region shorter "
+                                                        "than the 50 ms sampling period)"}
+
+
+# ----------------------------------------------------------------- timing ---
+
+def timed_steps(v, w, dev_in, steps, warmup, flush, profile=False):
+    """Runs warm-up + timed steps of one Validator; returns per-step ms."""
+    import torch
+    out = (torch.empty(w["n"], dtype=torch.uint8, device=v.device),
+           torch.empty(w["n"], dtype=torch.float64, device=v.device),
+           torch.empty(w["n"], dtype=torch.float64, device=v.device))
+
+    def step():
+        if w["kind"] == "indexed":
+            v.check_indexed(dev_in[0], dev_in[1], out=out)
+        else:
+            v.check_soa(dev_in[0], out=out)
+
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    v.raise_on_status()
+    if profile:
+        v.profile(True)
+        v.profile_read(reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    wall0 = time.time()
+    for i in range(steps):
+        flush.zero_()
+        starts[i].record()
+        step()
+        ends[i].record()
+    torch.cuda.synchronize()
+    wall1 = time.time()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    prof = v.profile_read(reset=True) if profile else None
+    if profile:
+        v.profile(False)
+    v.raise_on_status()
+    return ms, prof, (wall0, wall1), out
+
+
+def e2e_steps(v, w, steps, warmup):
+    """Public API on host data: pinned host inputs copied in, flags copied
+    out, every step."""
+    import torch
+    if w["kind"] == "indexed":
+        host = (torch.from_numpy(w["nodes"]).pin_memory(), torch.from_numpy(w["conn"]).pin_memory())
+    else:
+        host = (torch.from_numpy(w["X"]).pin_memory(),)
+    h2d = sum(t.numel() * t.element_size() for t in host)
+    d2h = w["n"]
+    for _ in range(warmup):
+        v.check_host(w["kind"], *host)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(steps):
+        flags = v.check_host(w["kind"], *host)
+    t1.record()
+    torch.cuda.synchronize()
+    v.raise_on_status()
+    ms = t0.elapsed_time(t1) / steps
+    return ms, h2d, d2h, flags
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu capture, if the kernel
+    source has not changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1706_01613_gb300", "csrc", rec["source"])
+    h = hashlib.sha256()
+    for part in [src, os.path.join(ROOT, "paper_1706_01613_gb300", "csrc", "hexval_internal.cuh")]:
+        with open(part, "rb") as f:
+            h.update(f.read())
+    if h.hexdigest()[:16] != rec.get("source_sha"):
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------ CPU oracle ----
+
+def oracle_rate(w, seconds, threads):
+    """The oracle (as it stands) on the same workload, repeated for about
+    `seconds`; returns (hex/s, threads, sample description)."""
+    import oracle
+    oracle.build()
+    reps, n_done, t0 = 0, 0, time.time()
+    while True:
+        if w["kind"] == "indexed":
+            oracle.check_indexed(w["nodes"], w["conn"], max_depth=w["depth"], threads=threads)
+        else:
+            oracle.check_soa(w["X"], max_depth=w["depth"], threads=threads)
+        reps += 1
+        n_done += w["n"]
+        if time.time() - t0 >= seconds:
+            break
+    dt = time.time() - t0
+    return n_done / dt, "%d full passes over the workload (%d hexes) in %.1f s" % (reps, n_done, dt)
+
+
+def reference_arm(args, w):
+    """--impl reference: the CPU oracle on the host cores, K steps of a bounded
+    sample each (sized from a calibration run so the whole run takes a few
+    minutes)."""
+    import oracle
+    oracle.build()
+    threads = oracle.max_threads()
+    k = 20_000
+    sub = _subset(w, k)
+    t0 = time.time()
+    _oracle_call(sub, threads)
+    rate = k / max(time.time() - t0, 1e-6)
+    budget = 120.0
+    per_step = max(1000, min(w["n"], int(rate * budget / max(1, args.steps + args.warmup))))
+    sub = _subset(w, per_step)
+    for _ in range(args.warmup):
+        _oracle_call(sub, threads)
+    t0 = time.time()
+    for _ in range(args.steps):
+        _oracle_call(sub, threads)
+    dt = time.time() - t0
+    value = per_step * args.steps / dt
+    sample = "first %d hexes of the workload per step, %d threads" % (per_step, threads)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w["name"], "sample_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def _subset(w, k):
+    k = min(k, w["n"])
+    if w["kind"] == "indexed":
+        return dict(w, conn=w["conn"][:k], n=k)
+    return dict(w, X=np.ascontiguousarray(w["X"][:, :, :k]), n=k)
+
+
+def _oracle_call(w, threads):
+    import oracle
+    if w["kind"] == "indexed":
+        return oracle.check_indexed(w["nodes"], w["conn"], max_depth=w["depth"], threads=threads)
+    return oracle.check_soa(w["X"], max_depth=w["depth"], threads=threads)
+
+
+# ------------------------------------------------------------------- main ---
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        w = workload(args.config, 0)
+        print(json.dumps(reference_arm(args, w)))
+        return 0
+
+    import torch
+    import torch.distributed as dist
+    from paper_1706_01613_gb300 import hexval as hv
+    from paper_1706_01613_gb300 import _build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    w = workload(args.config, rank)
+    if w["kind"] == "indexed":
+        dev_in = (torch.from_numpy(w["nodes"]).cuda(), torch.from_numpy(w["conn"]).cuda())
+    else:
+        dev_in = (torch.from_numpy(w["X"]).cuda(),)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    props = torch.cuda.get_device_properties(local)
+    bus = getattr(props, "pci_bus_id", None)
+
+    v32 = hv.Validator(precision="fp32", max_depth=w["depth"])
+    v64 = hv.Validator(precision="fp64", max_depth=w["depth"])
+
+    clocks = ClockSampler(bus)
+    if rank == 0:
+        clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    v32.stats(reset=True)
+    ms32, prof32, window, out32 = timed_steps(v32, w, dev_in, args.steps, args.warmup, flush,
+                                              profile=True)
+    st32 = v32.stats()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.stop()
+    total = sum(ms32)
+    if world > 1:
+        t = torch.tensor([total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    value = world * w["n"] * args.steps / (total / 1e3)
+    ms_step = total / args.steps
+
+    # plain FP64 form, same input, fewer steps (about 70x slower)
+    k64 = args.fp64_steps or max(3, args.steps // 50)
+    ms64, prof64, _, out64 = timed_steps(v64, w, dev_in, k64, max(3, args.warmup // 5), flush,
+                                         profile=True)
+    tot64 = sum(ms64)
+    if world > 1:
+        t = torch.tensor([tot64], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot64 = float(t.item())
+    value64 = world * w["n"] * k64 / (tot64 / 1e3)
+    same = bool(torch.equal(out32[0] & 0x7F, out64[0] & 0x7F))
+
+    # end to end through the public API with host buffers
+    e2e_ms, h2d, d2h, _ = e2e_steps(v32, w, args.e2e_steps, 3)
+    e2e_val = w["n"] / (e2e_ms / 1e3)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = world * w["n"] / (float(t.item()) / 1e3)
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel of the FP32-filtered step
+    phases = {k: v for k, v in prof32.items() if v[1] > 0}
+    dom = max(phases, key=lambda k: phases[k][0])
+    dom_ms = phases[dom][0] / phases[dom][1]
+    hbm, peak_kind = peaks()
+    if dom in ("bulk32", "nodes32"):
+        abytes = algorithmic_bytes(w)
+        if dom == "nodes32":
+            abytes = w["node_bytes"] + 32 * (w["node_bytes"] // 24)
+        achieved = abytes / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind + " (hbm_gbs)",
+                "traffic": traffic_for("bulk32_indexed" if w["kind"] == "indexed" else "bulk32_soa"),
+                "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": dom_ms}
+    else:
+        roof = {"bound": "alu", "kernel": dom, "avg_launch_ms": dom_ms}
+    share = {k: round(v[0] / sum(x[0] for x in phases.values()), 4) for k, v in phases.items()}
+
+    # FP64 form: FP64-pipe roofline (instructions of the FP64 unit per hex)
+    fp64_ops_per_hex = 345  # 36 edges + 36 sums + 20 x 9 triple products + 85 (Table t:Tsmall) + 8
+    p64 = {k: v for k, v in prof64.items() if v[1] > 0}
+    b64 = p64.get("bulk64", (0.0, 1))
+    b64_ms = b64[0] / max(1, b64[1])
+    fp64_rate = fp64_ops_per_hex * w["n"] / (b64_ms / 1e3) / 1e12
+    fp64_peak = 0.50  # T FP64 instructions/s, measured DFMA throughput on this machine's GB300
+
+    cpu = None
+    if world == 1:
+        import oracle
+        oracle.build()
+        thr = oracle.max_threads()
+        rate, sample = oracle_rate(w, args.cpu_seconds, thr)
+        cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample}
+
+    launches_per_step = sum(v[1] for v in phases.values()) / args.steps
+    rec = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (certified, f64/exact escalation)",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "n_hex": w["n"], "form": "fp32-filtered",
+                   "max_depth": w["depth"], "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas (one mesh per GPU, no collective)"},
+        "fp64": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": tot64 / k64,
+                 "flags_equal_fp32_form": same,
+                 "roofline": {"bound": "alu", "kernel": "bulk64", "achieved": fp64_rate,
+                              "peak": fp64_peak, "unit": "T FP64-inst/s",
+                              "frac": fp64_rate / fp64_peak, "ops_per_hex": fp64_ops_per_hex,
+                              "avg_launch_ms": b64_ms}},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "roofline": roof,
+        "phase_share": share,
+        "stats_fp32": st32,
+        "cpu_baseline": cpu,
+        "clocks": clocks.summary(*window),
+    }
+    print(json.dumps(rec))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -74,7 +74,15 @@ typedef struct {
   uint64_t queue_capacity; /* boxes per refinement level (default 2^23) */
   uint64_t max_nodes;      /* node capacity of the FP32 indexed path (default 2^24) */
   uint64_t exact_capacity; /* elements per batch for the exact tier (default 2^16) */
+  uint32_t options;        /* HEXVAL_OPT_* bits (default 0) */
+  uint32_t reserved[3];    /* must be 0 */
 } hexval_config;
+
+/* options: HEXVAL_OPT_PAIR32 runs the FP32 bulk pass with two elements per
+ * thread in packed f32x2 arithmetic instead of one element per thread in
+ * scalar FP32 (same results; a tuning knob: on the 128^3 mesh the scalar
+ * form measured faster). */
+enum { HEXVAL_OPT_PAIR32 = 1 };
 
 typedef struct {
   uint64_t elements;        /* elements processed since the last reset */
@@ -89,8 +97,8 @@ typedef struct {
 int hexval_config_default(hexval_config* cfg);
 
 /* Creates a handle on cfg->device and allocates all of its device scratch
- * (about 460 B x queue_capacity + 24 B x max_nodes + 9 B x max_batch with
- * the defaults: ~4.4 GB).  Returns HEXVAL_E_NOMEM if that fails. */
+ * (about 460 B x queue_capacity + 16 B x max_nodes + 4 B x max_batch + 39 MB
+ * with the defaults: ~4.2 GB).  Returns HEXVAL_E_NOMEM if that fails. */
 int hexval_create(const hexval_config* cfg, hexval_handle* out);
 
 /* Frees the handle's scratch (synchronises its device). */
@@ -125,6 +133,29 @@ int hexval_status(hexval_handle h, void* stream);
 
 /* Synchronises the stream and copies the counters; reset != 0 zeroes them. */
 int hexval_get_stats(hexval_handle h, hexval_stats* out, int reset, void* stream);
+
+/* Per-phase device time, measured with CUDA events recorded on the launch
+ * stream around each kernel of the call sequence (diagnostic; adds a few
+ * microseconds per call while enabled; do not enable during graph capture). */
+enum {
+  HEXVAL_PH_NODES32 = 0, /* FP64 nodes -> FP32 copy (FP32 form, indexed input) */
+  HEXVAL_PH_BULK32 = 1,  /* FP32 bulk pass */
+  HEXVAL_PH_BULK64 = 2,  /* FP64 bulk pass */
+  HEXVAL_PH_TAIL = 3,    /* FP64 redo of FP32 escalations and refinement */
+  HEXVAL_PH_EXACT = 4,   /* exact tier */
+  HEXVAL_PH_COUNT = 8
+};
+typedef struct {
+  double ms[HEXVAL_PH_COUNT];         /* accumulated device milliseconds */
+  uint64_t launches[HEXVAL_PH_COUNT]; /* timed launches */
+} hexval_profile;
+
+/* Turns phase timing on (on != 0) or off for the handle. */
+int hexval_profile_enable(hexval_handle h, int on);
+
+/* Waits for the recorded events, copies the accumulated times; reset != 0
+ * zeroes them. */
+int hexval_profile_read(hexval_handle h, hexval_profile* out, int reset);
 
 /* Static description of a code. */
 const char* hexval_strerror(int code);

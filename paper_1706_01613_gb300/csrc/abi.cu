@@ -2,13 +2,12 @@
 // the per-call launch sequence.
 //
 // One call = one or more batches of at most max_batch elements; per batch:
-//   memset(counters)
-//   [FP32 form]  bulk32 (all elements) -> bulk64 over the escalation list
-//   [FP64 form]  bulk64 (all elements)
-//   refine, levels 0 .. D-1 (each launch reads its box count on the device
-//                and returns at once when the level is empty)
-//   finalize (verdicts of refined elements)
-//   exact (elements whose signs could not be certified)
+//   [FP32 form, indexed]  nodes32 (once per call)
+//   bulk32 (FP32 form) or bulk64 (FP64 form) over all elements of the batch
+//   tail:  one cooperative launch that redoes the FP32 escalations in FP64,
+//          refines the undecided elements level by level and writes their
+//          verdicts
+//   exact: the exact tier, then the reset of the batch counters.
 // Nothing synchronises with the host, nothing allocates: a call can be
 // enqueued on any stream and captured into a CUDA graph.
 #include <cstdio>
@@ -20,11 +19,22 @@
 using hexval::Batch;
 using hexval::Scratch;
 
+// Event pairs for the optional per-phase timing.
+struct Profiler {
+  static constexpr int kPairs = 2048;
+  bool on = false;
+  cudaEvent_t ev[kPairs][2] = {};
+  int phase[kPairs] = {};
+  int head = 0, pending = 0;  // ring of recorded, unread pairs
+  hexval_profile acc = {};
+};
+
 struct hexval_ctx {
   hexval_config cfg;
   Scratch s;
   void* blocks[24];
   int nblocks;
+  Profiler prof;
 };
 
 namespace {
@@ -54,25 +64,55 @@ void free_all(hexval_ctx* h) {
   h->nblocks = 0;
 }
 
+void prof_drain(Profiler& P, int keep) {
+  while (P.pending > keep) {
+    int i = (P.head - P.pending + Profiler::kPairs) % Profiler::kPairs;
+    float ms = 0.f;
+    if (cudaEventSynchronize(P.ev[i][1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, P.ev[i][0], P.ev[i][1]) == cudaSuccess) {
+      P.acc.ms[P.phase[i]] += ms;
+      P.acc.launches[P.phase[i]] += 1;
+    }
+    cudaGetLastError();
+    --P.pending;
+  }
+}
+
+// Launches one phase, bracketed by timing events when profiling is on.
+template <typename F>
+cudaError_t phase(hexval_ctx* h, int ph, cudaStream_t st, F&& launch) {
+  Profiler& P = h->prof;
+  if (!P.on) return launch();
+  if (P.pending == Profiler::kPairs) prof_drain(P, Profiler::kPairs - 1);
+  int i = P.head;
+  cudaEventRecord(P.ev[i][0], st);
+  cudaError_t e = launch();
+  cudaEventRecord(P.ev[i][1], st);
+  P.phase[i] = ph;
+  P.head = (P.head + 1) % Profiler::kPairs;
+  ++P.pending;
+  return e;
+}
+
 int run_batches(hexval_ctx* h, Batch p, int64_t n_hex, cudaStream_t st) {
   const hexval_config& c = h->cfg;
   for (int64_t base = 0; base < n_hex; base += static_cast<int64_t>(c.max_batch)) {
     p.base = base;
     p.n = n_hex - base < static_cast<int64_t>(c.max_batch) ? n_hex - base
                                                             : static_cast<int64_t>(c.max_batch);
-    if (cudaMemsetAsync(h->s.cnt, 0, sizeof(hexval::Counters), st) != cudaSuccess)
+    const bool fp32 = c.precision == HEXVAL_FP32_FILTERED;
+    cudaError_t e = fp32 ? phase(h, HEXVAL_PH_BULK32, st, [&] { return hexval::launch_bulk32(p, st); })
+                         : phase(h, HEXVAL_PH_BULK64, st, [&] { return hexval::launch_bulk64(p, st); });
+    if (e == cudaSuccess)
+      e = phase(h, HEXVAL_PH_TAIL, st, [&] { return hexval::launch_tail(p, fp32, st); });
+    if (e == cudaSuccess)
+      e = phase(h, HEXVAL_PH_EXACT, st, [&] { return hexval::launch_exact(p, st); });
+    if (e != cudaSuccess) {
+      // the tail resets the counters; if it could not run, reset them here
+      cudaGetLastError();
+      cudaMemsetAsync(h->s.cnt, 0, sizeof(hexval::Counters), st);
       return HEXVAL_E_CUDA;
-    cudaError_t e;
-    if (c.precision == HEXVAL_FP32_FILTERED) {
-      if ((e = hexval::launch_bulk32(p, st)) != cudaSuccess) return HEXVAL_E_CUDA;
-      if ((e = hexval::launch_bulk64(p, true, st)) != cudaSuccess) return HEXVAL_E_CUDA;
-    } else {
-      if ((e = hexval::launch_bulk64(p, false, st)) != cudaSuccess) return HEXVAL_E_CUDA;
     }
-    for (int level = 0; level < c.max_depth; ++level)
-      if (hexval::launch_refine(p, level, st) != cudaSuccess) return HEXVAL_E_CUDA;
-    if (hexval::launch_finalize(p, st) != cudaSuccess) return HEXVAL_E_CUDA;
-    if (hexval::launch_exact(p, st) != cudaSuccess) return HEXVAL_E_CUDA;
   }
   return HEXVAL_OK;
 }
@@ -101,7 +141,9 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
   if (cfg->precision != HEXVAL_FP64 && cfg->precision != HEXVAL_FP32_FILTERED) return HEXVAL_E_ARG;
   if (cfg->max_batch == 0 || cfg->max_batch > (1ull << 31) || cfg->queue_capacity == 0 ||
       cfg->queue_capacity > (1ull << 31) || cfg->exact_capacity == 0 ||
-      cfg->exact_capacity > (1ull << 31) || cfg->max_nodes > (1ull << 31))
+      cfg->exact_capacity > (1ull << 31) || cfg->max_nodes > (1ull << 31) ||
+      (cfg->options & ~static_cast<uint32_t>(HEXVAL_OPT_PAIR32)) || cfg->reserved[0] ||
+      cfg->reserved[1] || cfg->reserved[2])
     return HEXVAL_E_ARG;
   hexval_ctx* h = new (std::nothrow) hexval_ctx();
   if (!h) return HEXVAL_E_NOMEM;
@@ -114,14 +156,14 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
   s.qcap = cfg->queue_capacity;
   s.exact_cap = cfg->exact_capacity;
   s.max_nodes = cfg->max_nodes;
-  s.exact_work_words = hexval::exact_work_words_per_worker() * hexval::exact_workers();
+  s.exact_work_words = hexval::exact_work_words();
   bool ok = alloc(h, &s.qcoef[0], 27 * s.qcap) && alloc(h, &s.qcoef[1], 27 * s.qcap) &&
             alloc(h, &s.qslot[0], s.qcap) && alloc(h, &s.qslot[1], s.qcap) &&
             alloc(h, &s.slot_elem, s.qcap) && alloc(h, &s.slot_state, s.qcap) &&
             alloc(h, &s.slot_lev, s.qcap) && alloc(h, &s.slot_e0, s.qcap) &&
             alloc(h, &s.slot_m0, s.qcap) && alloc(h, &s.esc, cfg->max_batch) &&
             alloc(h, &s.exact_list, s.exact_cap) && alloc(h, &s.exact_work, s.exact_work_words) &&
-            alloc(h, &s.node32, 8 * s.max_nodes) && alloc(h, &s.cnt, 1) &&
+            alloc(h, &s.node32, 4 * s.max_nodes) && alloc(h, &s.cnt, 1) &&
             alloc(h, &s.stats, 1) && alloc(h, &s.status, 1);
   if (!ok) {
     free_all(h);
@@ -144,6 +186,11 @@ int hexval_destroy(hexval_handle h) {
   if (!h) return HEXVAL_E_ARG;
   set_device(h);
   cudaDeviceSynchronize();
+  if (h->prof.ev[0][0])
+    for (int i = 0; i < Profiler::kPairs; ++i) {
+      cudaEventDestroy(h->prof.ev[i][0]);
+      cudaEventDestroy(h->prof.ev[i][1]);
+    }
   free_all(h);
   delete h;
   return HEXVAL_OK;
@@ -159,6 +206,7 @@ int hexval_check_soa(hexval_handle h, int64_t n_hex, const double* corners, uint
   p.soa = corners;
   p.stride = n_hex;
   p.indexed = 0;
+  p.pair32 = (h->cfg.options & HEXVAL_OPT_PAIR32) != 0;
   p.flags = flags;
   p.bmin = bmin;
   p.bmax = bmax;
@@ -184,13 +232,15 @@ int hexval_check_indexed(hexval_handle h, int64_t n_nodes, const double* nodes, 
   p.n_nodes = n_nodes;
   p.conn = conn;
   p.indexed = 1;
+  p.pair32 = (h->cfg.options & HEXVAL_OPT_PAIR32) != 0;
   p.flags = flags;
   p.bmin = bmin;
   p.bmax = bmax;
   p.max_depth = h->cfg.max_depth;
   p.s = h->s;
   if (h->cfg.precision == HEXVAL_FP32_FILTERED &&
-      hexval::launch_nodes32(p, st) != cudaSuccess)
+      phase(h, HEXVAL_PH_NODES32, st, [&] { return hexval::launch_nodes32(p, st); }) !=
+          cudaSuccess)
     return HEXVAL_E_CUDA;
   return run_batches(h, p, n_hex, st);
 }
@@ -224,6 +274,30 @@ int hexval_get_stats(hexval_handle h, hexval_stats* out, int reset, void* stream
   out->exact = s.exact;
   out->max_level_boxes = s.max_level_boxes;
   if (reset && cudaMemset(h->s.stats, 0, sizeof(s)) != cudaSuccess) return HEXVAL_E_CUDA;
+  return HEXVAL_OK;
+}
+
+int hexval_profile_enable(hexval_handle h, int on) {
+  if (!h) return HEXVAL_E_ARG;
+  if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;
+  Profiler& P = h->prof;
+  if (on && !P.ev[0][0]) {
+    for (int i = 0; i < Profiler::kPairs; ++i)
+      if (cudaEventCreate(&P.ev[i][0]) != cudaSuccess ||
+          cudaEventCreate(&P.ev[i][1]) != cudaSuccess)
+        return HEXVAL_E_CUDA;
+  }
+  if (!on) prof_drain(P, 0);
+  P.on = on != 0;
+  return HEXVAL_OK;
+}
+
+int hexval_profile_read(hexval_handle h, hexval_profile* out, int reset) {
+  if (!h || !out) return HEXVAL_E_ARG;
+  if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;
+  prof_drain(h->prof, 0);
+  *out = h->prof.acc;
+  if (reset) h->prof.acc = hexval_profile{};
   return HEXVAL_OK;
 }
 

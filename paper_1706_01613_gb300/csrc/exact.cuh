@@ -20,16 +20,16 @@
 // Working storage: per worker thread, 592 integers of up to 32 limbs in the
 // handle's scratch, interleaved across workers (limb w of worker t at
 // w * n_workers + t) so that a warp's accesses coalesce.
+#pragma once
+
 #include "hexval_internal.cuh"
 
 namespace hexval {
 
-namespace {
+namespace exact_tier {
 
 constexpr int kLimbsMax = 32;
-constexpr int kExactThreads = 64;
-constexpr int kExactBlocks = 8;
-constexpr int kWorkers = kExactThreads * kExactBlocks;
+constexpr int kWorkers = 512;  // threads that may work on the exact list at once
 constexpr int kStackInts = (kMaxDepth + 1) * 27;
 constexpr int kTempInts = 160;
 constexpr int kInts = kStackInts + kTempInts;
@@ -47,10 +47,12 @@ template <int NL>
 struct Big {
   const Ws& ws;
   __device__ void zero(uint32_t r) const {
+#pragma unroll 1
     for (int i = 0; i < NL; ++i) ws.w(r, i) = 0u;
   }
   // r = +-(m << sh), m < 2^53
   __device__ void set(uint32_t r, unsigned long long m, int sh, bool neg) const {
+    #pragma unroll 1
     for (int i = 0; i < NL; ++i) {
       int lo = 32 * i - sh;  // bit of m that lands at limb i, bit 0
       unsigned long long v = 0;
@@ -65,6 +67,7 @@ struct Big {
   }
   __device__ void negate(uint32_t r) const {
     unsigned long long c = 1;
+    #pragma unroll 1
     for (int i = 0; i < NL; ++i) {
       c += static_cast<uint32_t>(~ws.w(r, i));
       ws.w(r, i) = static_cast<uint32_t>(c);
@@ -74,6 +77,7 @@ struct Big {
   // r = a + b  (r may alias)
   __device__ void add(uint32_t r, uint32_t a, uint32_t b) const {
     unsigned long long c = 0;
+    #pragma unroll 1
     for (int i = 0; i < NL; ++i) {
       c += static_cast<unsigned long long>(ws.w(a, i)) + ws.w(b, i);
       ws.w(r, i) = static_cast<uint32_t>(c);
@@ -83,6 +87,7 @@ struct Big {
   // r = a - b
   __device__ void sub(uint32_t r, uint32_t a, uint32_t b) const {
     unsigned long long c = 1;
+    #pragma unroll 1
     for (int i = 0; i < NL; ++i) {
       c += static_cast<unsigned long long>(ws.w(a, i)) + static_cast<uint32_t>(~ws.w(b, i));
       ws.w(r, i) = static_cast<uint32_t>(c);
@@ -93,6 +98,7 @@ struct Big {
   __device__ void lin3(uint32_t r, uint32_t a, uint32_t wa, uint32_t b, uint32_t wb, uint32_t c,
                        uint32_t wc) const {
     unsigned long long carry = 0;
+    #pragma unroll 1
     for (int i = 0; i < NL; ++i) {
       unsigned long long acc = carry + static_cast<unsigned long long>(wa) * ws.w(a, i) +
                                static_cast<unsigned long long>(wb) * ws.w(b, i) +
@@ -104,10 +110,12 @@ struct Big {
   // r = a * b mod 2^W (r must not alias a or b)
   __device__ void mul(uint32_t r, uint32_t a, uint32_t b) const {
     zero(r);
+    #pragma unroll 1
     for (int i = 0; i < NL; ++i) {
       unsigned long long ai = ws.w(a, i);
       if (!ai) continue;
       unsigned long long carry = 0;
+#pragma unroll 1
       for (int j = 0; i + j < NL; ++j) {
         unsigned long long t = ai * ws.w(b, j) + ws.w(r, i + j) + carry;
         ws.w(r, i + j) = static_cast<uint32_t>(t);
@@ -118,6 +126,7 @@ struct Big {
   // -1, 0, +1
   __device__ int sign(uint32_t a) const {
     if (ws.w(a, NL - 1) >> 31) return -1;
+#pragma unroll 1
     for (int i = 0; i < NL; ++i)
       if (ws.w(a, i)) return 1;
     return 0;
@@ -153,6 +162,7 @@ struct Exact {
       B.mul(t0, A + d, cr + d);
       B.add(acc, acc, t0);
     }
+#pragma unroll 1
     for (int i = 0; i < NL; ++i) B.ws.w(r, i) = B.ws.w(acc, i);
   }
 
@@ -320,85 +330,57 @@ struct Exact {
   }
 };
 
-__global__ void __launch_bounds__(kExactThreads) exact_kernel(Batch p) {
+// Decides element e of the batch exactly and writes its flag (exact bit
+// set).  `worker` < kWorkers selects the working storage.
+__device__ __noinline__ void exact_element(const Batch& p, uint32_t e, uint32_t worker) {
   const Scratch& S = p.s;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    // per-batch counters are final here (stream order): fold them into stats
-    Stats* st = S.stats;
-    unsigned int boxes = 0, mx = 0;
-    for (int l = 1; l <= kMaxDepth + 1; ++l) {
-      boxes += S.cnt->level_count[l];
-      mx = max(mx, S.cnt->level_count[l]);
-    }
-    atomicAdd(&st->elements, static_cast<unsigned long long>(p.n));
-    atomicAdd(&st->escalated_fp64, static_cast<unsigned long long>(S.cnt->esc_count));
-    atomicAdd(&st->refined, static_cast<unsigned long long>(S.cnt->level_count[0]));
-    atomicAdd(&st->boxes, static_cast<unsigned long long>(boxes));
-    atomicAdd(&st->exact, static_cast<unsigned long long>(min(S.cnt->exact_count,
-                                                              static_cast<unsigned int>(S.exact_cap))));
-    atomicMax(&st->max_level_boxes, static_cast<unsigned long long>(mx));
-  }
-  const unsigned int n = min(S.cnt->exact_count, static_cast<unsigned int>(S.exact_cap));
-  const unsigned int t = blockIdx.x * blockDim.x + threadIdx.x;
-  Ws ws{S.exact_work, t};
-  for (unsigned int i = t; i < n; i += kWorkers) {
-    uint32_t e = S.exact_list[i];
-    int64_t g = p.base + e;
-    V3<double> X[8];
-    if (!load_element(p, g, X)) continue;  // cannot happen: checked by the bulk pass
-    unsigned long long M[24];
-    int q[24];
-    bool neg[24];
-    int qmin = 1 << 20, top = -(1 << 20);
-    for (int k = 0; k < 8; ++k)
-      for (int d = 0; d < 3; ++d) {
-        double v = d == 0 ? X[k].x : (d == 1 ? X[k].y : X[k].z);
-        unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
-        int ex = static_cast<int>((bits >> 52) & 0x7ff);
-        unsigned long long m = bits & 0xfffffffffffffull;
-        if (ex) m |= 1ull << 52;
-        int qq = (ex ? ex : 1) - 1075;
-        int idx = 3 * k + d;
-        neg[idx] = bits >> 63;
-        if (m) {
-          int tz = __ffsll(static_cast<long long>(m)) - 1;
-          m >>= tz;
-          qq += tz;
-          qmin = min(qmin, qq);
-          top = max(top, qq + 63 - __clzll(static_cast<long long>(m)));
-        }
-        M[idx] = m;
-        q[idx] = qq;
+  Ws ws{S.exact_work, worker};
+  int64_t g = p.base + e;
+  V3<double> X[8];
+  if (!load_element(p, g, X)) return;  // cannot happen: checked by the bulk pass
+  unsigned long long M[24];
+  int q[24];
+  bool neg[24];
+  int qmin = 1 << 20, top = -(1 << 20);
+  for (int k = 0; k < 8; ++k)
+    for (int d = 0; d < 3; ++d) {
+      double v = d == 0 ? X[k].x : (d == 1 ? X[k].y : X[k].z);
+      unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(v));
+      int ex = static_cast<int>((bits >> 52) & 0x7ff);
+      unsigned long long m = bits & 0xfffffffffffffull;
+      if (ex) m |= 1ull << 52;
+      int qq = (ex ? ex : 1) - 1075;
+      int idx = 3 * k + d;
+      neg[idx] = bits >> 63;
+      if (m) {
+        int tz = __ffsll(static_cast<long long>(m)) - 1;
+        m >>= tz;
+        qq += tz;
+        qmin = min(qmin, qq);
+        top = max(top, qq + 63 - __clzll(static_cast<long long>(m)));
       }
-    int Bbits = top >= qmin ? top - qmin + 1 : 0;
-    int sh[24];
-    for (int k = 0; k < 24; ++k) sh[k] = M[k] ? q[k] - qmin : 0;
-    int need = 3 * Bbits + 17 + 6 * p.max_depth;
-    int flag;
-    if (need <= 256)
-      flag = Exact<8>{Big<8>{ws}}.run(M, sh, neg, p.max_depth);
-    else if (need <= 512)
-      flag = Exact<16>{Big<16>{ws}}.run(M, sh, neg, p.max_depth);
-    else if (need <= 1024)
-      flag = Exact<32>{Big<32>{ws}}.run(M, sh, neg, p.max_depth);
-    else
-      flag = -1;
-    if (flag < 0) {
-      set_status(S.status, kSbRange);
-      flag = make_flag(kVUndecided, p.max_depth, 0);
+      M[idx] = m;
+      q[idx] = qq;
     }
-    p.flags[g] = static_cast<uint8_t>(flag | 0x80);
+  int Bbits = top >= qmin ? top - qmin + 1 : 0;
+  int sh[24];
+  for (int k = 0; k < 24; ++k) sh[k] = M[k] ? q[k] - qmin : 0;
+  int need = 3 * Bbits + 17 + 6 * p.max_depth;
+  int flag;
+  if (need <= 256)
+    flag = Exact<8>{Big<8>{ws}}.run(M, sh, neg, p.max_depth);
+  else if (need <= 512)
+    flag = Exact<16>{Big<16>{ws}}.run(M, sh, neg, p.max_depth);
+  else if (need <= 1024)
+    flag = Exact<32>{Big<32>{ws}}.run(M, sh, neg, p.max_depth);
+  else
+    flag = -1;
+  if (flag < 0) {
+    set_status(S.status, kSbRange);
+    flag = make_flag(kVUndecided, p.max_depth, 0);
   }
+  p.flags[g] = static_cast<uint8_t>(flag | 0x80);
 }
 
-}  // namespace
-
-uint64_t exact_work_words_per_worker() { return static_cast<uint64_t>(kInts) * kLimbsMax; }
-int exact_workers() { return kWorkers; }
-
-cudaError_t launch_exact(const Batch& p, cudaStream_t st) {
-  exact_kernel<<<kExactBlocks, kExactThreads, 0, st>>>(p);
-  return cudaGetLastError();
-}
-
+}  // namespace exact_tier
 }  // namespace hexval

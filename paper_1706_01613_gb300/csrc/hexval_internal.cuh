@@ -42,12 +42,16 @@ constexpr uint32_t kSbRange = 8u;
 
 constexpr int kMaxDepth = 15;
 
-// Counters zeroed at the start of every batch.
+// Per-batch counters.  They are zero when a batch starts: the last block of
+// the tail kernel resets them once every block is done with them (and the
+// handle creation zeroes them once).
 struct Counters {
   unsigned int level_count[kMaxDepth + 2];  // boxes queued per level; [0] = refined elements
   unsigned int esc_count;                   // FP32 -> FP64 escalation list
   unsigned int exact_count;                 // exact-tier list
-  unsigned int pad[13];
+  unsigned int arrive;                      // grid barrier of the tail kernel
+  unsigned int done;                        // blocks of the tail kernel that finished
+  unsigned int pad[11];
 };
 
 // Counters accumulated across calls (hexval_get_stats).
@@ -93,6 +97,7 @@ struct Batch {
   int64_t n_nodes;
   const int32_t* conn;
   int indexed;
+  int pair32;  // FP32 pass: two elements per thread with packed f32x2 math
   // outputs (indexed by base + e)
   uint8_t* flags;
   double* bmin;
@@ -131,6 +136,50 @@ __device__ __forceinline__ float det3(const V3<float>& A, const V3<float>& B,
   float cy = fmaf(B.z, C.x, -(B.x * C.z));
   float cz = fmaf(B.x, C.y, -(B.y * C.x));
   return fmaf(A.z, cz, fmaf(A.y, cy, A.x * cx));
+}
+
+// A pair of FP32 values, one per element of a pair processed by one thread,
+// computed with the packed f32x2 instructions of sm_100+ (one instruction for
+// both lanes: half the issue slots of scalar FP32 at the same FLOP rate).
+// Every operation rounds each lane exactly as its scalar counterpart.
+struct F2 {
+  float2 v;
+  __device__ __forceinline__ F2() {}
+  __device__ __forceinline__ explicit F2(float c) : v(make_float2(c, c)) {}
+  __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) {
+  F2 r;
+  r.v = __fadd2_rn(a.v, b.v);
+  return r;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) {
+  F2 r;
+  r.v = __fmul2_rn(a.v, b.v);
+  return r;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) {
+  unsigned long long x = *reinterpret_cast<unsigned long long*>(&a.v);
+  unsigned long long y = *reinterpret_cast<unsigned long long*>(&b.v), z;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(z) : "l"(x), "l"(y));
+  F2 r;
+  r.v = *reinterpret_cast<float2*>(&z);
+  return r;
+}
+__device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) {
+  F2 r;
+  r.v = __ffma2_rn(a.v, b.v, c.v);
+  return r;
+}
+using ::fma;  // keep the FP64 / FP32 overloads visible next to the F2 one
+// det(A, B, C) for two elements: cross product with separate products and a
+// subtraction (2 roundings per term, as the scalar FMA form), then the dot
+// product (3 roundings).
+__device__ __forceinline__ F2 det3(const V3<F2>& A, const V3<F2>& B, const V3<F2>& C) {
+  F2 cx = B.y * C.z - B.z * C.y;
+  F2 cy = B.z * C.x - B.x * C.z;
+  F2 cz = B.x * C.y - B.y * C.x;
+  return fma(A.z, cz, fma(A.y, cy, A.x * cx));
 }
 
 // Node k (Appendix A order) at the reference corner (xi, eta, zeta) in {0,1}^3.
@@ -259,17 +308,17 @@ __device__ __forceinline__ void coefficients_from_edges(const V3<T> a[4], const 
     ey[u] = (s.edgeC[u] + s.edgeC[u + 2]) + (s.edgeC[8 + 2 * u] + s.edgeC[9 + 2 * u]);
     ex[u] = (s.edgeC[4 + u] + s.edgeC[6 + u]) + (s.edgeC[8 + u] + s.edgeC[10 + u]);
   }
-  const T three = T(3), five = T(5);
-  s.face[0] = fma(-three, cz[0], ez[0]);
-  s.face[1] = fma(-three, cz[1], ez[1]);
-  s.face[2] = fma(-three, cy[0], ey[0]);
-  s.face[3] = fma(-three, cy[1], ey[1]);
-  s.face[4] = fma(-three, cx[0], ex[0]);
-  s.face[5] = fma(-three, cx[1], ex[1]);
+  const T m3 = T(-3), m5 = T(-5);
+  s.face[0] = fma(m3, cz[0], ez[0]);
+  s.face[1] = fma(m3, cz[1], ez[1]);
+  s.face[2] = fma(m3, cy[0], ey[0]);
+  s.face[3] = fma(m3, cy[1], ey[1]);
+  s.face[4] = fma(m3, cx[0], ex[0]);
+  s.face[5] = fma(m3, cx[1], ex[1]);
   // centre: all 12 samples and all 8 corners
   T esum = (ez[0] + ez[1]) + ((s.edgeC[8] + s.edgeC[9]) + (s.edgeC[10] + s.edgeC[11]));
   T csum = cz[0] + cz[1];
-  s.centre = fma(-five, csum, esum);
+  s.centre = fma(m5, csum, esum);
 }
 
 // Unscaled coefficient in tensor order from the scaled classes.
@@ -373,6 +422,44 @@ __device__ __forceinline__ void set_status(uint32_t* status, uint32_t bit) {
   atomicOr(status, bit);
 }
 
+// Loads that bypass the (non-coherent) L1: data written by other blocks of
+// the same launch.
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident), with
+// a bounded wait: after kSpinLimit polls the block records kSbTimeout and
+// goes on (results of that call are then reported as unreliable by the
+// status, and the kernel still terminates).
+constexpr long long kSpinLimit = 1ll << 26;
+__device__ __forceinline__ void grid_barrier(unsigned int* arrive, unsigned int& epoch,
+                                             uint32_t* status) {
+  __syncthreads();
+  ++epoch;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(arrive, 1u);
+    const unsigned int target = epoch * gridDim.x;
+    long long spins = 0;
+    while (ld_acquire(arrive) < target) {
+      if (++spins > kSpinLimit) {
+        atomicOr(status, kSbTimeout);
+        break;
+      }
+      __nanosleep(100);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------- element loading ------
 // Loads the 8 nodes (24 coordinates) of element g of the batch.  Returns
 // false (and sets the status) when a connectivity entry is out of range.
@@ -423,13 +510,11 @@ __device__ __forceinline__ void edges_from_nodes(const V3<T> X[8], V3<T> a[4], V
 
 // ------------------------------------------------------------- launches ----
 // Host-side launchers (defined in the .cu files).
-cudaError_t launch_bulk64(const Batch& p, bool from_list, cudaStream_t st);
+cudaError_t launch_bulk64(const Batch& p, cudaStream_t st);
 cudaError_t launch_bulk32(const Batch& p, cudaStream_t st);
 cudaError_t launch_nodes32(const Batch& p, cudaStream_t st);
-cudaError_t launch_refine(const Batch& p, int level, cudaStream_t st);
-cudaError_t launch_finalize(const Batch& p, cudaStream_t st);
+cudaError_t launch_tail(const Batch& p, bool from_list, cudaStream_t st);
 cudaError_t launch_exact(const Batch& p, cudaStream_t st);
-uint64_t exact_work_words_per_worker();
-int exact_workers();
+uint64_t exact_work_words();
 
 }  // namespace hexval

@@ -1,0 +1,297 @@
+// Everything after the bulk pass, in two launches.
+//
+// tail_kernel, one persistent cooperative launch:
+//  phase E  (FP32 form) the elements escalated by the FP32 bulk pass are
+//           redone in FP64 (element64.cuh);
+//  levels   refinement of undecided elements (Sec. 6, recursive_subdivision),
+//           breadth first, one level per grid-wide step;
+//  phase F  verdicts of the refined elements.
+// Grid-wide steps are separated by a bounded grid barrier.  Every box count
+// is read after a barrier, so all blocks take the same branches; with
+// nothing to refine the kernel returns at its first instructions.
+//
+// exact_kernel: the exact tier (exact.cuh) for elements whose signs could
+// not be certified; its last block folds the batch counters into the
+// statistics and resets them for the next batch.
+//
+// Refinement.  Level d holds boxes of depth d whose corners are certainly
+// positive and which are certainly not certified.  Each is split at 1/2
+// along xi, eta and zeta (quadratic de Casteljau: a row (p0, p1, p2) becomes
+// (p0, (p0+p1)/2, (p0+2p1+p2)/4, (p1+p2)/2, p2); the left child keeps the
+// first three, the right child the last three) and its 8 children of depth
+// d+1 are classified:
+//   a corner coefficient certainly <= 0          -> element INVALID at d+1
+//   all 27 certainly > 0                         -> child certified
+//   corners certainly > 0, another certainly <=0 -> child queued for d+2
+//                                                   (or the cap is hit)
+//   a sign that the error bound cannot settle    -> element goes exact.
+// INVALID found on a level wins over anything else found on that level, which
+// gives the order-independent verdict (shallowest level with a non-positive
+// corner) whatever the order in which boxes are processed.
+//
+// Error bound of every coefficient at depth d: E0 + d 2^-49 M0, E0 bounding
+// the depth-0 coefficients and M0 >= |every coefficient| (children are convex
+// combinations; one level adds at most 6 roundings of size u M0).
+#include "element64.cuh"
+#include "exact.cuh"
+
+namespace hexval {
+
+namespace {
+
+constexpr int kTailThreads = 128;
+
+// Inlining of the per-item routines into the persistent kernel.
+#ifndef HEXVAL_TAIL_INLINE
+#define HEXVAL_TAIL_INLINE __forceinline__
+#endif
+
+__device__ __forceinline__ void split5(double p0, double p1, double p2, double q[5]) {
+  double s = p0 + p1, t = p1 + p2;
+  q[0] = p0;
+  q[1] = 0.5 * s;
+  q[2] = 0.25 * (s + t);
+  q[3] = 0.5 * t;
+  q[4] = p2;
+}
+
+// One box of level `level` (act = false: idle lane).  Called by all lanes.
+__device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool act, unsigned int idx) {
+  const Scratch& S = p.s;
+  const int in = level & 1, out = in ^ 1;
+  const int child_level = level + 1;
+  const bool last = child_level >= p.max_depth;
+  uint32_t slot = act ? ldcg(S.qslot[in] + idx) : 0u;
+  if (act) act = !(ldcg(S.slot_state + slot) & (kStInvalid | kStAmbig | kStOverflow));
+  double G[5][5][5];
+  uint32_t key = 0;
+  if (act) {
+    const double* qc = S.qcoef[in];
+    double A[27];
+#pragma unroll
+    for (int t = 0; t < 27; ++t) A[t] = ldcg(qc + static_cast<uint64_t>(t) * S.qcap + idx);
+    double E = fma(static_cast<double>(child_level) * 0x1p-49, ldcg(S.slot_m0 + slot),
+                   ldcg(S.slot_e0 + slot));
+    key = dhi(E);
+    double P1[5][3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        double q[5];
+        split5(A[tix(0, j, k)], A[tix(1, j, k)], A[tix(2, j, k)], q);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) P1[i][j][k] = q[i];
+      }
+    double P2[5][5][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        double q[5];
+        split5(P1[i][0][k], P1[i][1][k], P1[i][2][k], q);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) P2[i][j][k] = q[j];
+      }
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) split5(P2[i][j][0], P2[i][j][1], P2[i][j][2], G[i][j]);
+  }
+  uint32_t bits = 0;   // element state bits found by this box
+  uint32_t queue = 0;  // children to queue
+  if (act) {
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
+      bool nonpos = false, amb = false, notcert = false, amb2 = false;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            Sign3 q = sign_d(G[sx + i][sy + j][sz + k], key);
+            if ((i != 1) && (j != 1) && (k != 1)) {
+              nonpos |= q.nonpos;
+              amb |= !(q.nonpos | q.pos);
+            } else {
+              notcert |= q.nonpos;
+              amb2 |= !(q.nonpos | q.pos);
+            }
+          }
+      if (nonpos) {
+        bits |= kStInvalid;
+      } else if (amb) {
+        bits |= kStAmbig;
+      } else if (notcert) {
+        if (last)
+          bits |= kStCap;
+        else
+          queue |= 1u << o;
+      } else if (amb2) {
+        bits |= kStAmbig;
+      }
+    }
+    if (bits & kStInvalid) queue = 0;  // the element is decided on this level
+  }
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    bool want = (queue >> o) & 1u;
+    unsigned int pos = warp_append(&S.cnt->level_count[child_level], want);
+    if (want) {
+      if (pos < S.qcap) {
+        const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
+        double* dst = S.qcoef[out];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+              dst[static_cast<uint64_t>(tix(i, j, k)) * S.qcap + pos] = G[sx + i][sy + j][sz + k];
+        S.qslot[out][pos] = slot;
+      } else {
+        bits |= kStOverflow;
+      }
+    }
+  }
+  if (act) {
+    if (bits) atomicOr(&S.slot_state[slot], bits);
+    if (bits & kStOverflow) set_status(S.status, kSbQueue);
+    S.slot_lev[slot] = static_cast<uint32_t>(child_level);
+  }
+}
+
+// Verdict of refined element `s`; elements that need the exact tier are
+// appended to its list.  Called by all lanes.
+__device__ HEXVAL_TAIL_INLINE void finalize_slot(const Batch& p, bool act, unsigned int s) {
+  const Scratch& S = p.s;
+  uint32_t st = act ? ldcg(S.slot_state + s) : 0u;
+  uint32_t lev = act ? ldcg(S.slot_lev + s) : 0u;
+  uint32_t e = act ? ldcg(S.slot_elem + s) : 0u;
+  bool to_exact = act && !(st & kStInvalid) && (st & (kStAmbig | kStOverflow));
+  unsigned int pos = warp_append(&S.cnt->exact_count, to_exact);
+  if (!act) return;
+  uint8_t flag;
+  if (st & kStInvalid) {
+    flag = make_flag(kVInvalid, lev, 0);
+  } else if (to_exact) {
+    if (pos < S.exact_cap) {
+      S.exact_list[pos] = e;
+      return;
+    }
+    set_status(S.status, kSbQueue);
+    flag = make_flag(kVUndecided, p.max_depth, 0);
+  } else if (st & kStCap) {
+    flag = make_flag(kVUndecided, p.max_depth, 0);
+  } else {
+    flag = make_flag(kVValid, lev, 0);
+  }
+  p.flags[p.base + e] = flag;
+}
+
+// Work items of a grid-wide step are dealt to warps round robin over the
+// blocks first, so that a short list is spread over all SMs (each warp takes
+// 32 consecutive items; the trip count is uniform within a warp).
+#define FOR_EACH_ITEM(n, i, act)                                                     \
+  for (unsigned int w_ = blockIdx.x + gridDim.x * (threadIdx.x >> 5), i = 0, act = 0; \
+       w_ * 32u < (n); w_ += gridDim.x * (blockDim.x >> 5))                           \
+    if ((i = w_ * 32u + (threadIdx.x & 31u)), (act = i < (n)), true)
+
+__device__ HEXVAL_TAIL_INLINE void fp64_item(const Batch& p, bool act, uint32_t e) {
+  fp64_element(p, act, e);
+}
+
+__global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from_list) {
+  const Scratch& S = p.s;
+  Counters* C = S.cnt;
+  const unsigned int n_esc = from_list ? ldcg(&C->esc_count) : 0u;
+  if (n_esc == 0 && ldcg(&C->level_count[0]) == 0) return;  // nothing to refine
+  unsigned int epoch = 0;
+  if (n_esc) {  // phase E
+    FOR_EACH_ITEM(n_esc, i, act) fp64_item(p, act, act ? ldcg(S.esc + i) : 0u);
+    grid_barrier(&C->arrive, epoch, S.status);
+  }
+  const unsigned int n0 = min(ldcg(&C->level_count[0]), static_cast<unsigned int>(S.qcap));
+  if (n0 == 0) return;
+  for (int level = 0; level < p.max_depth; ++level) {
+    const unsigned int n = min(ldcg(&C->level_count[level]),
+                               static_cast<unsigned int>(S.qcap));
+    if (n == 0) break;
+    FOR_EACH_ITEM(n, i, act) refine_box(p, level, act, i);
+    grid_barrier(&C->arrive, epoch, S.status);
+  }
+  FOR_EACH_ITEM(n0, i, act) finalize_slot(p, act, i);
+}
+
+// Exact tier over the list, then (last block) statistics and the reset of
+// the batch counters for the next batch.
+constexpr int kExactThreads = 64;
+constexpr int kExactBlocks = exact_tier::kWorkers / kExactThreads;
+
+__global__ void __launch_bounds__(kExactThreads) exact_kernel(Batch p) {
+  const Scratch& S = p.s;
+  Counters* C = S.cnt;
+  const unsigned int nx = min(ldcg(&C->exact_count), static_cast<unsigned int>(S.exact_cap));
+  const unsigned int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (unsigned int i = tid; i < nx; i += exact_tier::kWorkers)
+    exact_tier::exact_element(p, ldcg(S.exact_list + i), tid);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int done = atomicAdd(&C->done, 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      Stats* st = S.stats;
+      unsigned long long boxes = 0, mx = 0;
+      for (int l = 1; l <= kMaxDepth + 1; ++l) {
+        unsigned long long c = ldcg(&C->level_count[l]);
+        boxes += c;
+        mx = c > mx ? c : mx;
+      }
+      atomicAdd(&st->elements, static_cast<unsigned long long>(p.n));
+      atomicAdd(&st->escalated_fp64, static_cast<unsigned long long>(ldcg(&C->esc_count)));
+      atomicAdd(&st->refined, static_cast<unsigned long long>(ldcg(&C->level_count[0])));
+      atomicAdd(&st->boxes, boxes);
+      atomicAdd(&st->exact, static_cast<unsigned long long>(nx));
+      atomicMax(&st->max_level_boxes, mx);
+      unsigned int* w = reinterpret_cast<unsigned int*>(C);
+      for (unsigned int k = 0; k < sizeof(Counters) / sizeof(unsigned int); ++k) w[k] = 0u;
+      __threadfence();
+    }
+  }
+}
+
+int tail_blocks() {
+  static int blocks = 0;
+  if (!blocks) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tail_kernel, kTailThreads, 0);
+    blocks = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+  }
+  return blocks;
+}
+
+}  // namespace
+
+uint64_t exact_work_words() {
+  return static_cast<uint64_t>(exact_tier::kInts) * exact_tier::kLimbsMax * exact_tier::kWorkers;
+}
+
+cudaError_t launch_tail(const Batch& p, bool from_list, cudaStream_t st) {
+  Batch arg = p;
+  int fl = from_list ? 1 : 0;
+  void* args[] = {&arg, &fl};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(tail_kernel), dim3(tail_blocks()),
+                                     dim3(kTailThreads), args, 0, st);
+}
+
+cudaError_t launch_exact(const Batch& p, cudaStream_t st) {
+  exact_kernel<<<kExactBlocks, kExactThreads, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace hexval

@@ -20,23 +20,31 @@ CODES = {0: "HEXVAL_OK", -1: "HEXVAL_E_ARG", -2: "HEXVAL_E_NOMEM", -3: "HEXVAL_E
          -4: "HEXVAL_E_INDEX", -5: "HEXVAL_E_QUEUE", -6: "HEXVAL_E_TIMEOUT",
          -7: "HEXVAL_E_RANGE"}
 FP64, FP32_FILTERED = 0, 1
+OPT_PAIR32 = 1  # hexval_config.options: packed f32x2 FP32 bulk pass
 VALID, INVALID, UNDECIDED, NONFINITE = 1, 2, 3, 4
 
 # every function declared in include/hexval.h (the CPU test checks the list)
 EXPORTS = ("hexval_config_default", "hexval_create", "hexval_destroy", "hexval_check_soa",
-           "hexval_check_indexed", "hexval_status", "hexval_get_stats", "hexval_strerror")
+           "hexval_check_indexed", "hexval_status", "hexval_get_stats", "hexval_profile_enable",
+           "hexval_profile_read", "hexval_strerror")
+PHASES = ("nodes32", "bulk32", "bulk64", "tail", "exact", "-", "-", "-")
 
 
 class Config(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("device", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_depth", ctypes.c_int32),
                 ("max_batch", ctypes.c_uint64), ("queue_capacity", ctypes.c_uint64),
-                ("max_nodes", ctypes.c_uint64), ("exact_capacity", ctypes.c_uint64)]
+                ("max_nodes", ctypes.c_uint64), ("exact_capacity", ctypes.c_uint64),
+                ("options", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("elements", "escalated_fp64", "refined", "boxes", "exact", "max_level_boxes")]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8)]
 
 
 class HexvalError(RuntimeError):
@@ -73,6 +81,8 @@ def load(build_if_missing=False):
     lib.hexval_check_indexed.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, vp]
     lib.hexval_status.argtypes = [vp, vp]
     lib.hexval_get_stats.argtypes = [vp, ctypes.POINTER(Stats), ctypes.c_int, vp]
+    lib.hexval_profile_enable.argtypes = [vp, ctypes.c_int]
+    lib.hexval_profile_read.argtypes = [vp, ctypes.POINTER(Profile), ctypes.c_int]
     lib.hexval_strerror.argtypes = [ctypes.c_int]
     lib.hexval_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -214,6 +224,17 @@ class Validator:
         rc = self.status(stream)
         if rc != HEXVAL_OK:
             raise HexvalError(rc, "device status")
+
+    def profile(self, on=True):
+        """Per-phase CUDA-event timing on the launch stream (diagnostic)."""
+        _check(self._lib.hexval_profile_enable(self._h, int(bool(on))), "hexval_profile_enable")
+
+    def profile_read(self, reset=False):
+        """{phase: (milliseconds, launches)} accumulated while profiling."""
+        p = Profile()
+        _check(self._lib.hexval_profile_read(self._h, ctypes.byref(p), int(reset)),
+               "hexval_profile_read")
+        return {name: (p.ms[i], p.launches[i]) for i, name in enumerate(PHASES) if name != "-"}
 
     def stats(self, reset=False, stream=None):
         s = Stats()

@@ -1,0 +1,228 @@
+"""Continuous-batching validation server on one GPU.
+
+Requests (meshes of very different sizes) arrive over time.  The server keeps
+a fixed set of slots; each slot owns one library handle (its refinement
+queue and exact-tier scratch stay on the device) and one CUDA stream.  A
+request is admitted as soon as a slot is free and its device footprint
+(inputs + outputs) fits in the HBM budget next to the requests already in
+flight; admitted requests overlap on the device (copy in, bulk pass, tail,
+copy out, all on the slot's stream).  Admission is first come, first served;
+a request larger than the whole budget is rejected.
+
+Latency = GPU completion time (an event on the slot's stream, read against
+an event recorded when the run started) minus the arrival time.
+
+The scheduling logic (`Scheduler`) is plain host code and is tested on the
+CPU with a fake executor; `GpuExecutor` runs the work through the C ABI.
+"""
+import collections
+import heapq
+import math
+import time
+
+import numpy as np
+
+
+class Request:
+    __slots__ = ("id", "kind", "arrays", "n", "arrival", "bytes", "result", "done", "admitted")
+
+    def __init__(self, rid, kind, arrays, n, arrival):
+        self.id = rid
+        self.kind = kind          # "soa": (corners,), "indexed": (nodes, conn)
+        self.arrays = arrays      # host arrays (pinned torch tensors for the GPU executor)
+        self.n = int(n)           # elements
+        self.arrival = float(arrival)
+        in_bytes = sum(int(a.numel() * a.element_size()) if hasattr(a, "numel")
+                       else int(a.nbytes) for a in arrays)
+        self.bytes = in_bytes + 17 * self.n  # + flags, bmin, bmax
+        self.result = None
+        self.done = None
+        self.admitted = None
+
+
+class Scheduler:
+    """FIFO admission under a slot count and a byte budget."""
+
+    def __init__(self, slots, budget_bytes):
+        self.free_slots = list(range(slots))
+        self.budget = int(budget_bytes)
+        self.in_use = 0
+        self.pending = collections.deque()
+        self.rejected = []
+
+    def arrive(self, req):
+        if req.bytes > self.budget:
+            self.rejected.append(req)
+        else:
+            self.pending.append(req)
+
+    def admissible(self):
+        """Pops and returns (slot, request) pairs that can start now."""
+        out = []
+        while self.pending and self.free_slots:
+            req = self.pending[0]
+            if self.in_use + req.bytes > self.budget:
+                break
+            self.pending.popleft()
+            slot = self.free_slots.pop()
+            self.in_use += req.bytes
+            out.append((slot, req))
+        return out
+
+    def release(self, slot, req):
+        self.in_use -= req.bytes
+        self.free_slots.append(slot)
+
+
+def run_stream(requests, executor, slots, budget_bytes, now=time.perf_counter, idle=None):
+    """Serves `requests` (sorted by arrival, times in seconds from the start)
+    on `executor`; returns the scheduler (for the rejected list)."""
+    sched = Scheduler(slots, budget_bytes)
+    order = sorted(requests, key=lambda r: r.arrival)
+    t0 = now()
+    executor.start()
+    nxt = 0
+    inflight = {}
+    while nxt < len(order) or sched.pending or inflight:
+        t = now() - t0
+        while nxt < len(order) and order[nxt].arrival <= t:
+            sched.arrive(order[nxt])
+            nxt += 1
+        for slot, req in sched.admissible():
+            req.admitted = t
+            executor.submit(slot, req)
+            inflight[slot] = req
+        for slot in list(inflight):
+            if executor.poll(slot):
+                req = inflight.pop(slot)
+                req.done = executor.finish(slot, req)
+                sched.release(slot, req)
+        if idle is not None:
+            idle()
+    return sched
+
+
+def latency_summary(requests):
+    lat = np.array([r.done - r.arrival for r in requests if r.done is not None])
+    hexes = sum(r.n for r in requests if r.done is not None)
+    if not len(lat):
+        return {}
+    span = max(r.done for r in requests if r.done is not None) - min(r.arrival for r in requests)
+    return {"requests": int(len(lat)), "hexes": int(hexes),
+            "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "max_ms": float(lat.max() * 1e3),
+            "hex_per_s": float(hexes / span) if span > 0 else None}
+
+
+class GpuExecutor:
+    """Runs requests through the library, one handle and stream per slot."""
+
+    def __init__(self, slots, precision="fp32", max_depth=8, **caps):
+        import torch
+        from . import hexval as hv
+        self.torch = torch
+        self.v = [hv.Validator(precision=precision, max_depth=max_depth, **caps)
+                  for _ in range(slots)]
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.events = [None] * slots
+        self.buffers = [None] * slots
+        self.t0 = None
+
+    def start(self):
+        torch = self.torch
+        torch.cuda.synchronize()
+        self.t0 = torch.cuda.Event(enable_timing=True)
+        self.t0.record()
+        self.t0_host = time.perf_counter()
+        torch.cuda.synchronize()
+
+    def submit(self, slot, req):
+        torch = self.torch
+        s = self.streams[slot]
+        with torch.cuda.stream(s):
+            if req.kind == "soa":
+                X = req.arrays[0]
+                dev = (X.to("cuda", non_blocking=True),)
+            else:
+                dev = tuple(a.to("cuda", non_blocking=True) for a in req.arrays)
+            out = (torch.empty(req.n, dtype=torch.uint8, device="cuda"),
+                   torch.empty(req.n, dtype=torch.float64, device="cuda"),
+                   torch.empty(req.n, dtype=torch.float64, device="cuda"))
+            if req.kind == "soa":
+                self.v[slot].check_soa(dev[0], out=out, stream=s)
+            else:
+                self.v[slot].check_indexed(dev[0], dev[1], out=out, stream=s)
+            host = tuple(torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in out)
+            for h, d in zip(host, out):
+                h.copy_(d, non_blocking=True)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(s)
+        self.events[slot] = ev
+        self.buffers[slot] = (dev, out, host)
+
+    def poll(self, slot):
+        return self.events[slot].query()
+
+    def finish(self, slot, req):
+        ev = self.events[slot]
+        ev.synchronize()
+        _, _, host = self.buffers[slot]
+        req.result = tuple(h.numpy() for h in host)
+        self.buffers[slot] = None
+        done = self.t0_host + self.t0.elapsed_time(ev) / 1e3
+        return done - self.t0_host
+
+    def status(self):
+        return [v.status() for v in self.v]
+
+    def close(self):
+        for v in self.v:
+            v.close()
+
+
+# ------------------------------------------------------ request streams ----
+
+class Pool:
+    """Pinned host inputs that requests slice: SoA pools of independent
+    elements (perturbed cubes, affine mixture) and one large structured grid
+    whose first n hexes (and the nodes they use) form an indexed request."""
+
+    def __init__(self, max_n, seed=20175000):
+        import torch
+        from . import synth
+        self.torch = torch
+        self.max_n = int(max_n)
+        self.soa = {1: torch.from_numpy(synth.perturbed_cubes(self.max_n, seed=seed + 1)).pin_memory(),
+                    3: torch.from_numpy(synth.affine_mixture(self.max_n, seed=seed + 3)[0]).pin_memory()}
+        a = max(2, int(math.ceil(self.max_n ** (1.0 / 3.0))))
+        nodes, conn = synth.structured_grid(a, a, a, seed=seed + 2)
+        self.nodes = torch.from_numpy(nodes).pin_memory()
+        self.conn = torch.from_numpy(conn).pin_memory()
+        self.node_hi = np.maximum.accumulate(conn.max(axis=1))
+
+    def request(self, rid, kind, n, arrival, offset=0):
+        torch = self.torch
+        n = int(min(n, self.max_n))
+        if kind == 2:
+            n = min(n, self.conn.shape[0])
+            hi = int(self.node_hi[n - 1]) + 1
+            return Request(rid, "indexed", (self.nodes[:hi], self.conn[:n]), n, arrival)
+        off = int(offset) % max(1, self.max_n - n + 1)
+        X = self.soa[kind]
+        dst = torch.empty((8, 3, n), dtype=torch.float64, pin_memory=True)
+        dst.copy_(X[:, :, off:off + n])
+        return Request(rid, "soa", (dst,), n, arrival)
+
+
+def poisson_stream(pool, n_requests, rate, seed, size_min=100, size_max=10_000_000):
+    """Requests with sizes log-uniform in [size_min, size_max] (capped by the
+    pool), generator kinds 1-3 uniformly, Poisson arrivals at `rate`/s."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate, n_requests)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    sizes = np.exp(rng.uniform(math.log(size_min), math.log(size_max), n_requests))
+    kinds = rng.integers(1, 4, n_requests)
+    offs = rng.integers(0, 1 << 30, n_requests)
+    return [pool.request(i, int(kinds[i]), int(sizes[i]), float(arrivals[i]), int(offs[i]))
+            for i in range(n_requests)]

@@ -1,0 +1,93 @@
+"""Host-side logic of the serving loop (no GPU): FIFO admission under the
+slot count and the HBM byte budget, rejection of requests larger than the
+budget, continuous batching (new requests start while others run)."""
+import numpy as np
+
+from paper_1706_01613_gb300 import serve
+
+
+class FakeArray:
+    def __init__(self, nbytes):
+        self.nbytes = nbytes
+
+
+class FakeExecutor:
+    """Completes a request `dur` simulated seconds after it was submitted."""
+
+    def __init__(self, clock, dur):
+        self.clock, self.dur = clock, dur
+        self.running = {}
+        self.log = []
+
+    def start(self):
+        pass
+
+    def submit(self, slot, req):
+        self.running[slot] = (req, self.clock.t + self.dur(req))
+        self.log.append(("start", req.id, slot, self.clock.t, dict(self.running)))
+
+    def poll(self, slot):
+        return self.running[slot][1] <= self.clock.t
+
+    def finish(self, slot, req):
+        _, end = self.running.pop(slot)
+        self.log.append(("end", req.id, slot, end))
+        return end
+
+
+class Clock:
+    def __init__(self):
+        self.t = 0.0
+
+    def now(self):
+        return self.t
+
+    def tick(self):
+        self.t += 0.001
+
+
+def _reqs(sizes, arrivals):
+    return [serve.Request(i, "soa", (FakeArray(s),), 1, a) for i, (s, a) in enumerate(zip(sizes, arrivals))]
+
+
+def test_budget_and_slots_limit_concurrency():
+    clk = Clock()
+    ex = FakeExecutor(clk, lambda r: 0.05)
+    reqs = _reqs([400, 400, 400, 400], [0.0, 0.0, 0.0, 0.0])
+    sched = serve.run_stream(reqs, ex, slots=3, budget_bytes=1000, now=clk.now, idle=clk.tick)
+    starts = [e for e in ex.log if e[0] == "start"]
+    # 417 bytes each (400 + 17 outputs): only two fit in 1000 bytes at once
+    assert max(len(e[4]) for e in starts) == 2
+    assert not sched.rejected and all(r.done is not None for r in reqs)
+    assert sched.in_use == 0 and len(sched.free_slots) == 3
+
+
+def test_too_large_is_rejected_and_fifo_order_kept():
+    clk = Clock()
+    ex = FakeExecutor(clk, lambda r: 0.01)
+    reqs = _reqs([100, 5000, 100, 100], [0.0, 0.001, 0.002, 0.003])
+    sched = serve.run_stream(reqs, ex, slots=1, budget_bytes=1000, now=clk.now, idle=clk.tick)
+    assert [r.id for r in sched.rejected] == [1]
+    order = [e[1] for e in ex.log if e[0] == "start"]
+    assert order == [0, 2, 3]
+
+
+def test_continuous_batching_admits_while_running():
+    """A short request arriving while a long one runs starts at once on a
+    free slot and finishes first."""
+    clk = Clock()
+    ex = FakeExecutor(clk, lambda r: 1.0 if r.id == 0 else 0.01)
+    reqs = _reqs([100, 100], [0.0, 0.1])
+    serve.run_stream(reqs, ex, slots=2, budget_bytes=10_000, now=clk.now, idle=clk.tick)
+    assert reqs[1].admitted < reqs[0].done and reqs[1].done < reqs[0].done
+    s = serve.latency_summary(reqs)
+    assert s["requests"] == 2 and s["p50_ms"] > 0
+
+
+def test_latency_summary_percentiles():
+    reqs = _reqs([1] * 100, [0.0] * 100)
+    for i, r in enumerate(reqs):
+        r.done = (i + 1) * 1e-3
+    s = serve.latency_summary(reqs)
+    assert abs(s["p50_ms"] - np.percentile(np.arange(1, 101), 50)) < 1e-9
+    assert abs(s["p99_ms"] - np.percentile(np.arange(1, 101), 99)) < 1e-9
