@@ -1,0 +1,109 @@
+"""Autotuner for the launch configuration of the validity check.
+
+For a workload shape (precision, input kind, size) it times every candidate
+configuration of the handle (FP32 bulk pass scalar or packed f32x2; bulk
+block size) on a sample input through the C ABI, with CUDA events on the
+launch stream, and keeps the fastest.  Results are cached per device name in
+a JSON file (default ~/.cache/hexval/tune.json, or $HEXVAL_TUNE_CACHE) so a
+shape is tuned once.
+
+    cfg = tune.best_config("fp32", "indexed", n_hex, sample=(nodes, conn))
+    v = hexval.Validator(precision="fp32", **cfg)
+"""
+import json
+import math
+import os
+
+from . import hexval as hv
+
+CACHE = os.environ.get("HEXVAL_TUNE_CACHE",
+                       os.path.join(os.path.expanduser("~"), ".cache", "hexval", "tune.json"))
+
+
+def candidates(precision):
+    """Configurations to try (keyword arguments of hexval.Validator)."""
+    blocks = [0, 64, 128, 256]  # 0: the library default
+    out = []
+    for bt in blocks:
+        if precision == "fp32":
+            out.append(dict(options=0, bulk_threads=bt))
+            out.append(dict(options=hv.OPT_PAIR32, bulk_threads=bt))
+        else:
+            out.append(dict(options=0, bulk_threads=bt))
+    return out
+
+
+def _key(precision, kind, n):
+    import torch
+    name = torch.cuda.get_device_name()
+    bucket = int(round(math.log2(max(1, n))))
+    return "%s|%s|%s|2^%d" % (name, precision, kind, bucket)
+
+
+def _load_cache(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save_cache(path, data):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def time_config(cfg, precision, kind, dev_inputs, reps=20, warmup=3, max_depth=8, **caps):
+    """Median milliseconds of one call with configuration `cfg`."""
+    import torch
+    v = hv.Validator(precision=precision, max_depth=max_depth, **cfg, **caps)
+    try:
+        n = dev_inputs[-1].shape[0] if kind == "indexed" else dev_inputs[0].shape[2]
+        out = (torch.empty(n, dtype=torch.uint8, device="cuda"),
+               torch.empty(n, dtype=torch.float64, device="cuda"),
+               torch.empty(n, dtype=torch.float64, device="cuda"))
+
+        def call():
+            if kind == "indexed":
+                v.check_indexed(dev_inputs[0], dev_inputs[1], out=out)
+            else:
+                v.check_soa(dev_inputs[0], out=out)
+
+        for _ in range(warmup):
+            call()
+        torch.cuda.synchronize()
+        v.raise_on_status()
+        ms = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            call()
+            b.record()
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        ms.sort()
+        return ms[len(ms) // 2]
+    finally:
+        v.close()
+
+
+def best_config(precision, kind, n, dev_inputs, cache=CACHE, retune=False, **caps):
+    """The fastest candidate for this shape (tuned on `dev_inputs`, cached)."""
+    data = _load_cache(cache) if cache else {}
+    key = _key(precision, kind, n)
+    if key in data and not retune:
+        return dict(data[key]["config"])
+    results = []
+    for cfg in candidates(precision):
+        results.append((time_config(cfg, precision, kind, dev_inputs, **caps), cfg))
+    results.sort(key=lambda r: r[0])
+    best_ms, best = results[0]
+    data[key] = {"config": best, "ms": best_ms,
+                 "all": [{"config": c, "ms": m} for m, c in results]}
+    if cache:
+        _save_cache(cache, data)
+    return dict(best)
