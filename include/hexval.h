@@ -157,6 +157,33 @@ int hexval_profile_enable(hexval_handle h, int on);
  * zeroes them. */
 int hexval_profile_read(hexval_handle h, hexval_profile* out, int reset);
 
+/* FP64 check of independent elements that allocates nothing, for callers
+ * that cannot call cudaMalloc (for instance code running inside a host
+ * callback or a driver layer that owns every allocation, or a process whose
+ * device memory pool is fixed after start-up).  The paper has no counterpart:
+ * this is a packaging of hexval_check_soa (FP64 form) for such callers.
+ *
+ * It needs no handle.  Its scratch (refinement queue, refinement state,
+ * exact-tier list and stacks, counters, status) is one static device array of
+ * about 47 MB that every device which loads the library holds until the
+ * process exits.  Limits: n_hex <= 16384 per call (larger calls return
+ * HEXVAL_E_ARG and enqueue nothing); refinement levels of at most 16384
+ * boxes (more boxes send the elements concerned to the exact tier);
+ * max_depth 0..15.  Arguments as hexval_check_soa; status_bits, if not NULL,
+ * is a device word that receives the call's device-status bits (1 bad index,
+ * 2 queue or list full, 4 bounded wait gave up, 8 exact-tier range), written
+ * in stream order.
+ *
+ * The first call on a device looks the array up (cudaGetSymbolAddress) and
+ * zeroes its counters; make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and must
+ * be serialised by the caller.  No cudaMalloc, cudaFree or allocating
+ * library routine is called. */
+int hexval_check_soa_noalloc(int64_t n_hex, const double* corners, uint8_t* flags, double* bmin,
+                             double* bmax, int32_t max_depth, uint32_t* status_bits,
+                             void* stream);
+
 /* Static description of a code. */
 const char* hexval_strerror(int code);
 

@@ -26,7 +26,7 @@ VALID, INVALID, UNDECIDED, NONFINITE = 1, 2, 3, 4
 # every function declared in include/hexval.h (the CPU test checks the list)
 EXPORTS = ("hexval_config_default", "hexval_create", "hexval_destroy", "hexval_check_soa",
            "hexval_check_indexed", "hexval_status", "hexval_get_stats", "hexval_profile_enable",
-           "hexval_profile_read", "hexval_strerror")
+           "hexval_profile_read", "hexval_check_soa_noalloc", "hexval_strerror")
 PHASES = ("nodes32", "bulk32", "bulk64", "tail", "exact", "-", "-", "-")
 
 
@@ -83,6 +83,7 @@ def load(build_if_missing=False):
     lib.hexval_get_stats.argtypes = [vp, ctypes.POINTER(Stats), ctypes.c_int, vp]
     lib.hexval_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.hexval_profile_read.argtypes = [vp, ctypes.POINTER(Profile), ctypes.c_int]
+    lib.hexval_check_soa_noalloc.argtypes = [i64, vp, vp, vp, vp, ctypes.c_int32, vp, vp]
     lib.hexval_strerror.argtypes = [ctypes.c_int]
     lib.hexval_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -241,6 +242,24 @@ class Validator:
         _check(self._lib.hexval_get_stats(self._h, ctypes.byref(s), int(reset),
                                           _stream_ptr(stream)), "hexval_get_stats")
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+NOALLOC_MAX_HEX = 16384
+
+
+def check_soa_noalloc(corners, out, max_depth=8, status_bits=None, stream=None):
+    """FP64 check through the allocation-free entry point, for callers that
+    cannot allocate device memory (no handle; at most 16384 elements per
+    call).  `out` = the caller's (flags, bmin, bmax) CUDA tensors (bmin and
+    bmax may be None); `status_bits` = optional int32 CUDA tensor of one
+    element that receives the call's device-status bits."""
+    lib = load()
+    n = corners.shape[2]
+    p = Validator._ptr
+    rc = lib.hexval_check_soa_noalloc(n, p(corners), p(out[0]), p(out[1]), p(out[2]),
+                                      int(max_depth), p(status_bits), _stream_ptr(stream))
+    _check(rc, "hexval_check_soa_noalloc")
+    return out
 
 
 def verdict(flags):
