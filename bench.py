@@ -227,6 +227,20 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# --------------------------------------------------------- multi-GPU ------
+
+def aggregate(total_ms, n_units, steps, world, dist=None, device="cpu"):
+    """Whole-job throughput of a weak-scaling run: every rank processed
+    n_units per step; the job time is the slowest rank's.  Returns
+    (units/s over all ranks, max total ms)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * n_units * steps / (total_ms / 1e3), total_ms
+
+
 # ------------------------------------------------------------ CPU oracle ----
 
 def oracle_rate(w, seconds, threads):
@@ -282,6 +296,25 @@ def reference_arm(args, w):
                     "d2h_bytes_per_step": 0}}
 
 
+def serving_run(precision, rate, n_requests, pool, slots=4, budget=40 << 30, seed=20175000):
+    """One continuous-batching run: Poisson arrivals at `rate`/s, sizes
+    log-uniform in [100, pool size]; returns the latency summary."""
+    from paper_1706_01613_gb300 import serve
+    reqs = serve.poisson_stream(pool, n_requests, rate, seed=seed + int(rate),
+                                size_max=pool.max_n)
+    ex = serve.GpuExecutor(slots, precision=precision, max_depth=8, queue_capacity=1 << 21,
+                           max_batch=1 << 24, max_nodes=1 << 24, exact_capacity=1 << 14)
+    try:
+        sched = serve.run_stream(reqs, ex, slots=slots, budget_bytes=budget)
+        bad = [s for s in ex.status() if s != 0]
+    finally:
+        ex.close()
+    out = serve.latency_summary(reqs)
+    out.update({"rate_per_s": rate, "rejected": len(sched.rejected), "status_errors": len(bad),
+                "precision": precision, "slots": slots, "hbm_budget_gb": budget / 2**30})
+    return out
+
+
 def _subset(w, k):
     k = min(k, w["n"])
     if w["kind"] == "indexed":
@@ -308,6 +341,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--serve", action="store_true",
+                    help="sweep Poisson arrival rates of the serving workload instead")
+    ap.add_argument("--serve-max-n", type=int, default=1_000_000)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -331,6 +367,18 @@ def main():
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
+    if args.serve:
+        from paper_1706_01613_gb300 import serve
+        pool = serve.Pool(args.serve_max_n)
+        sweep = []
+        for precision in ("fp32", "fp64"):
+            for rate in (10, 30, 100, 300, 1000, 2000):
+                n_req = int(min(400, max(40, 5 * rate)))
+                sweep.append(serving_run(precision, rate, n_req, pool))
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "mode": "serving sweep",
+                              "sizes": [100, args.serve_max_n], "sweep": sweep}))
+        return 0
     w = workload(args.config, rank)
     if w["kind"] == "indexed":
         dev_in = (torch.from_numpy(w["nodes"]).cuda(), torch.from_numpy(w["conn"]).cuda())
@@ -357,33 +405,19 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.stop()
-    total = sum(ms32)
-    if world > 1:
-        t = torch.tensor([total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = world * w["n"] * args.steps / (total / 1e3)
+    value, total = aggregate(sum(ms32), w["n"], args.steps, world, dist, "cuda")
     ms_step = total / args.steps
 
     # plain FP64 form, same input, fewer steps (about 70x slower)
     k64 = args.fp64_steps or max(3, args.steps // 50)
     ms64, prof64, _, out64 = timed_steps(v64, w, dev_in, k64, max(3, args.warmup // 5), flush,
                                          profile=True)
-    tot64 = sum(ms64)
-    if world > 1:
-        t = torch.tensor([tot64], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot64 = float(t.item())
-    value64 = world * w["n"] * k64 / (tot64 / 1e3)
+    value64, tot64 = aggregate(sum(ms64), w["n"], k64, world, dist, "cuda")
     same = bool(torch.equal(out32[0] & 0x7F, out64[0] & 0x7F))
 
     # end to end through the public API with host buffers
     e2e_ms, h2d, d2h, _ = e2e_steps(v32, w, args.e2e_steps, 3)
-    e2e_val = w["n"] / (e2e_ms / 1e3)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = world * w["n"] / (float(t.item()) / 1e3)
+    e2e_val, _ = aggregate(e2e_ms, w["n"], 1, world, dist, "cuda")
 
     if rank != 0:
         dist.destroy_process_group()
@@ -423,6 +457,11 @@ def main():
         rate, sample = oracle_rate(w, args.cpu_seconds, thr)
         cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample}
 
+    # serving: continuous batching of requests of very different sizes
+    from paper_1706_01613_gb300 import serve
+    pool = serve.Pool(args.serve_max_n)
+    latency = serving_run("fp32", 300, 150, pool)
+
     launches_per_step = sum(v[1] for v in phases.values()) / args.steps
     rec = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -445,6 +484,7 @@ def main():
         "phase_share": share,
         "stats_fp32": st32,
         "cpu_baseline": cpu,
+        "latency": latency,
         "clocks": clocks.summary(*window),
     }
     print(json.dumps(rec))

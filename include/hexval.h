@@ -75,7 +75,9 @@ typedef struct {
   uint64_t max_nodes;      /* node capacity of the FP32 indexed path (default 2^24) */
   uint64_t exact_capacity; /* elements per batch for the exact tier (default 2^16) */
   uint32_t options;        /* HEXVAL_OPT_* bits (default 0) */
-  uint32_t reserved[3];    /* must be 0 */
+  uint32_t bulk_threads;   /* threads per block of the bulk kernels: 0 (default: 256
+                              scalar, 128 packed), 64, 128 or 256 */
+  uint32_t reserved[2];    /* must be 0 */
 } hexval_config;
 
 /* options: HEXVAL_OPT_PAIR32 runs the FP32 bulk pass with two elements per

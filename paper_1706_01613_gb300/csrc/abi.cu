@@ -143,7 +143,9 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
       cfg->queue_capacity > (1ull << 31) || cfg->exact_capacity == 0 ||
       cfg->exact_capacity > (1ull << 31) || cfg->max_nodes > (1ull << 31) ||
       (cfg->options & ~static_cast<uint32_t>(HEXVAL_OPT_PAIR32)) || cfg->reserved[0] ||
-      cfg->reserved[1] || cfg->reserved[2])
+      cfg->reserved[1] ||
+      (cfg->bulk_threads != 0 && cfg->bulk_threads != 64 && cfg->bulk_threads != 128 &&
+       cfg->bulk_threads != 256))
     return HEXVAL_E_ARG;
   hexval_ctx* h = new (std::nothrow) hexval_ctx();
   if (!h) return HEXVAL_E_NOMEM;
@@ -207,6 +209,7 @@ int hexval_check_soa(hexval_handle h, int64_t n_hex, const double* corners, uint
   p.stride = n_hex;
   p.indexed = 0;
   p.pair32 = (h->cfg.options & HEXVAL_OPT_PAIR32) != 0;
+  p.bulk_threads = static_cast<int>(h->cfg.bulk_threads);
   p.flags = flags;
   p.bmin = bmin;
   p.bmax = bmax;
@@ -233,6 +236,7 @@ int hexval_check_indexed(hexval_handle h, int64_t n_nodes, const double* nodes, 
   p.conn = conn;
   p.indexed = 1;
   p.pair32 = (h->cfg.options & HEXVAL_OPT_PAIR32) != 0;
+  p.bulk_threads = static_cast<int>(h->cfg.bulk_threads);
   p.flags = flags;
   p.bmin = bmin;
   p.bmax = bmax;

@@ -381,36 +381,67 @@ __global__ void __launch_bounds__(256) nodes32_kernel(const double* nodes, int64
   out[i] = make_float4(x, y, z, bad ? 1.f : 0.f);
 }
 
+// Two nodes per thread with 16-byte loads (nodes 16-byte aligned).
+__global__ void __launch_bounds__(256) nodes32x2_kernel(const double2* nodes, int64_t n_nodes,
+                                                        float4* out) {
+  int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t i = 2 * t;
+  if (i >= n_nodes) return;
+  if (i + 1 < n_nodes) {
+    double2 a = __ldg(nodes + 3 * t), b = __ldg(nodes + 3 * t + 1), c = __ldg(nodes + 3 * t + 2);
+    bool bad0 = false, bad1 = false;
+    float x0 = d2f_int(a.x, bad0), y0 = d2f_int(a.y, bad0), z0 = d2f_int(b.x, bad0);
+    float x1 = d2f_int(b.y, bad1), y1 = d2f_int(c.x, bad1), z1 = d2f_int(c.y, bad1);
+    out[i] = make_float4(x0, y0, z0, bad0 ? 1.f : 0.f);
+    out[i + 1] = make_float4(x1, y1, z1, bad1 ? 1.f : 0.f);
+  } else {
+    const double* q = reinterpret_cast<const double*>(nodes) + 3 * i;
+    bool bad = false;
+    float x = d2f_int(__ldg(q), bad), y = d2f_int(__ldg(q + 1), bad), z = d2f_int(__ldg(q + 2), bad);
+    out[i] = make_float4(x, y, z, bad ? 1.f : 0.f);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_bulk64(const Batch& p, cudaStream_t st) {
   if (p.n <= 0) return cudaSuccess;
-  unsigned int blocks = static_cast<unsigned int>((p.n + kBulkThreads - 1) / kBulkThreads);
-  bulk64_kernel<<<blocks, kBulkThreads, 0, st>>>(p);
+  const int bt = p.bulk_threads ? p.bulk_threads : kBulkThreads;
+  unsigned int blocks = static_cast<unsigned int>((p.n + bt - 1) / bt);
+  bulk64_kernel<<<blocks, bt, 0, st>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_bulk32(const Batch& p, cudaStream_t st) {
   if (p.n <= 0) return cudaSuccess;
   if (p.pair32) {
+    const int bt = p.bulk_threads ? min(p.bulk_threads, kPairThreads) : kPairThreads;
     int64_t threads = (p.n + 1) / 2;
-    unsigned int blocks = static_cast<unsigned int>((threads + kPairThreads - 1) / kPairThreads);
+    unsigned int blocks = static_cast<unsigned int>((threads + bt - 1) / bt);
     if (p.indexed)
-      bulk32x2_kernel<true><<<blocks, kPairThreads, 0, st>>>(p);
+      bulk32x2_kernel<true><<<blocks, bt, 0, st>>>(p);
     else
-      bulk32x2_kernel<false><<<blocks, kPairThreads, 0, st>>>(p);
+      bulk32x2_kernel<false><<<blocks, bt, 0, st>>>(p);
     return cudaGetLastError();
   }
-  unsigned int blocks = static_cast<unsigned int>((p.n + kBulkThreads - 1) / kBulkThreads);
+  const int bt = p.bulk_threads ? p.bulk_threads : kBulkThreads;
+  unsigned int blocks = static_cast<unsigned int>((p.n + bt - 1) / bt);
   if (p.indexed)
-    bulk32_kernel<true><<<blocks, kBulkThreads, 0, st>>>(p);
+    bulk32_kernel<true><<<blocks, bt, 0, st>>>(p);
   else
-    bulk32_kernel<false><<<blocks, kBulkThreads, 0, st>>>(p);
+    bulk32_kernel<false><<<blocks, bt, 0, st>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_nodes32(const Batch& p, cudaStream_t st) {
   if (p.n_nodes <= 0) return cudaSuccess;
+  if (reinterpret_cast<uintptr_t>(p.nodes) % 16 == 0) {
+    int64_t threads = (p.n_nodes + 1) / 2;
+    unsigned int blocks = static_cast<unsigned int>((threads + 255) / 256);
+    nodes32x2_kernel<<<blocks, 256, 0, st>>>(reinterpret_cast<const double2*>(p.nodes),
+                                             p.n_nodes, reinterpret_cast<float4*>(p.s.node32));
+    return cudaGetLastError();
+  }
   unsigned int blocks = static_cast<unsigned int>((p.n_nodes + 255) / 256);
   nodes32_kernel<<<blocks, 256, 0, st>>>(p.nodes, p.n_nodes,
                                          reinterpret_cast<float4*>(p.s.node32));

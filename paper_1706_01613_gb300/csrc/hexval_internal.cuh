@@ -97,7 +97,8 @@ struct Batch {
   int64_t n_nodes;
   const int32_t* conn;
   int indexed;
-  int pair32;  // FP32 pass: two elements per thread with packed f32x2 math
+  int pair32;        // FP32 pass: two elements per thread with packed f32x2 math
+  int bulk_threads;  // block size of the bulk kernels (0: default)
   // outputs (indexed by base + e)
   uint8_t* flags;
   double* bmin;

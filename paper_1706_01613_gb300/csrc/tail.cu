@@ -34,6 +34,7 @@
 // combinations; one level adds at most 6 roundings of size u M0).
 #include "element64.cuh"
 #include "exact.cuh"
+#include "warp_items.cuh"
 
 namespace hexval {
 
@@ -135,11 +136,24 @@ __device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool ac
     }
     if (bits & kStInvalid) queue = 0;  // the element is decided on this level
   }
+  // one atomic per warp for all the children the warp queues
+  const unsigned int lane = threadIdx.x & 31u;
+  const unsigned int cnt = __popc(queue);
+  unsigned int incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    unsigned int v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= static_cast<unsigned int>(d)) incl += v;
+  }
+  const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned int pos = 0;
+  if (total) {
+    if (lane == 31) pos = atomicAdd(&S.cnt->level_count[child_level], total);
+    pos = __shfl_sync(0xffffffffu, pos, 31) + incl - cnt;
+  }
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
-    bool want = (queue >> o) & 1u;
-    unsigned int pos = warp_append(&S.cnt->level_count[child_level], want);
-    if (want) {
+    if ((queue >> o) & 1u) {
       if (pos < S.qcap) {
         const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
         double* dst = S.qcoef[out];
@@ -154,6 +168,7 @@ __device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool ac
       } else {
         bits |= kStOverflow;
       }
+      ++pos;
     }
   }
   if (act) {
@@ -203,14 +218,30 @@ __device__ HEXVAL_TAIL_INLINE void fp64_item(const Batch& p, bool act, uint32_t 
   fp64_element(p, act, e);
 }
 
+// Steps with at most this many items per warp use the warp-cooperative
+// routines (latency), larger ones one item per thread (throughput).
+constexpr unsigned int kWarpItemsMax = 8;
+
+// Items dealt to warps one at a time, round robin over the blocks first.
+#define FOR_EACH_WARP_ITEM(n, i)                                                    \
+  for (unsigned int i = blockIdx.x + gridDim.x * (threadIdx.x >> 5); i < (n);      \
+       i += gridDim.x * (blockDim.x >> 5))
+
 __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from_list) {
   const Scratch& S = p.s;
   Counters* C = S.cnt;
   const unsigned int n_esc = from_list ? ldcg(&C->esc_count) : 0u;
   if (n_esc == 0 && ldcg(&C->level_count[0]) == 0) return;  // nothing to refine
+  __shared__ double wsm[kTailThreads / 32][kWarpScratch];
+  double* mysm = wsm[threadIdx.x >> 5];
+  const unsigned int warp_items = kWarpItemsMax * gridDim.x * (blockDim.x >> 5);
   unsigned int epoch = 0;
   if (n_esc) {  // phase E
-    FOR_EACH_ITEM(n_esc, i, act) fp64_item(p, act, act ? ldcg(S.esc + i) : 0u);
+    if (n_esc <= warp_items) {
+      FOR_EACH_WARP_ITEM(n_esc, i) fp64_element_warp(p, ldcg(S.esc + i), mysm);
+    } else {
+      FOR_EACH_ITEM(n_esc, i, act) fp64_item(p, act, act ? ldcg(S.esc + i) : 0u);
+    }
     grid_barrier(&C->arrive, epoch, S.status);
   }
   const unsigned int n0 = min(ldcg(&C->level_count[0]), static_cast<unsigned int>(S.qcap));
@@ -219,7 +250,11 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
     const unsigned int n = min(ldcg(&C->level_count[level]),
                                static_cast<unsigned int>(S.qcap));
     if (n == 0) break;
-    FOR_EACH_ITEM(n, i, act) refine_box(p, level, act, i);
+    if (n <= warp_items) {
+      FOR_EACH_WARP_ITEM(n, i) refine_box_warp(p, level, i, mysm);
+    } else {
+      FOR_EACH_ITEM(n, i, act) refine_box(p, level, act, i);
+    }
     grid_barrier(&C->arrive, epoch, S.status);
   }
   FOR_EACH_ITEM(n0, i, act) finalize_slot(p, act, i);

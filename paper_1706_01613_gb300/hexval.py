@@ -35,7 +35,8 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("max_depth", ctypes.c_int32),
                 ("max_batch", ctypes.c_uint64), ("queue_capacity", ctypes.c_uint64),
                 ("max_nodes", ctypes.c_uint64), ("exact_capacity", ctypes.c_uint64),
-                ("options", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 3)]
+                ("options", ctypes.c_uint32), ("bulk_threads", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 2)]
 
 
 class Stats(ctypes.Structure):

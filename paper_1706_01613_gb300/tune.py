@@ -22,14 +22,11 @@ CACHE = os.environ.get("HEXVAL_TUNE_CACHE",
 
 def candidates(precision):
     """Configurations to try (keyword arguments of hexval.Validator)."""
-    blocks = [0, 64, 128, 256]  # 0: the library default
     out = []
-    for bt in blocks:
-        if precision == "fp32":
-            out.append(dict(options=0, bulk_threads=bt))
+    for bt in (64, 128, 256):
+        out.append(dict(options=0, bulk_threads=bt))
+        if precision == "fp32" and bt <= 128:
             out.append(dict(options=hv.OPT_PAIR32, bulk_threads=bt))
-        else:
-            out.append(dict(options=0, bulk_threads=bt))
     return out
 
 
@@ -91,7 +88,7 @@ def time_config(cfg, precision, kind, dev_inputs, reps=20, warmup=3, max_depth=8
         v.close()
 
 
-def best_config(precision, kind, n, dev_inputs, cache=CACHE, retune=False, **caps):
+def best_config(precision, kind, n, dev_inputs, cache=CACHE, retune=False, reps=20, **caps):
     """The fastest candidate for this shape (tuned on `dev_inputs`, cached)."""
     data = _load_cache(cache) if cache else {}
     key = _key(precision, kind, n)
@@ -99,7 +96,7 @@ def best_config(precision, kind, n, dev_inputs, cache=CACHE, retune=False, **cap
         return dict(data[key]["config"])
     results = []
     for cfg in candidates(precision):
-        results.append((time_config(cfg, precision, kind, dev_inputs, **caps), cfg))
+        results.append((time_config(cfg, precision, kind, dev_inputs, reps=reps, **caps), cfg))
     results.sort(key=lambda r: r[0])
     best_ms, best = results[0]
     data[key] = {"config": best, "ms": best_ms,

@@ -309,3 +309,33 @@ def test_scalar_and_packed_fp32_agree(kind):
     _compare("fp32", gb[:3], want)
     a.close()
     b.close()
+
+
+def test_autotuner_picks_a_candidate_and_stays_exact(tmp_path):
+    from paper_1706_01613_gb300 import tune
+    nodes, conn = synth.structured_grid(40, 40, 40, sigma=0.15, seed=80)
+    dev = (torch.from_numpy(nodes).cuda(), torch.from_numpy(conn).cuda())
+    cache = str(tmp_path / "tune.json")
+    best = tune.best_config("fp32", "indexed", len(conn), dev, cache=cache, reps=3, **CAPS)
+    assert best in tune.candidates("fp32")
+    assert tune.best_config("fp32", "indexed", len(conn), dev, cache=cache, **CAPS) == best
+    v = hv.Validator(precision="fp32", max_depth=8, **best, **CAPS)
+    got = [t.cpu().numpy() for t in v.check_indexed(*dev)]
+    _compare("fp32", got, oracle.check_indexed(nodes, conn, max_depth=8))
+    v.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_indexed_nodes_not_16_byte_aligned(validators, prec):
+    """A node array that starts 8 bytes past a 16-byte boundary (odd node
+    count too) takes the scalar conversion path and gives the same flags."""
+    nodes, conn = synth.structured_grid(12, 9, 7, sigma=0.3, seed=33)
+    buf = torch.zeros(nodes.size + 1, dtype=torch.float64, device="cuda")
+    buf[1:] = torch.from_numpy(nodes.reshape(-1)).cuda()
+    N = buf[1:].view(-1, 3)
+    assert N.data_ptr() % 16 == 8
+    v = validators[(prec, 8)]
+    f, lo, hi = v.check_indexed(N, torch.from_numpy(conn).cuda())
+    assert v.status() == 0
+    _compare(prec, (f.cpu().numpy(), lo.cpu().numpy(), hi.cpu().numpy()),
+             oracle.check_indexed(nodes, conn, max_depth=8))
