@@ -80,11 +80,13 @@ typedef struct {
   uint32_t reserved[2];    /* must be 0 */
 } hexval_config;
 
-/* options: HEXVAL_OPT_PAIR32 runs the FP32 bulk pass with two elements per
- * thread in packed f32x2 arithmetic instead of one element per thread in
- * scalar FP32 (same results; a tuning knob: on the 128^3 mesh the scalar
- * form measured faster). */
-enum { HEXVAL_OPT_PAIR32 = 1 };
+/* options (tuning knobs, same results):
+ *  HEXVAL_OPT_PAIR32   the FP32 bulk pass with two elements per thread in
+ *                      packed f32x2 arithmetic instead of one per thread;
+ *  HEXVAL_OPT_PREFETCH the indexed FP32 bulk pass on a persistent grid that
+ *                      loads each thread's next connectivity row ahead
+ *                      (ignored with HEXVAL_OPT_PAIR32). */
+enum { HEXVAL_OPT_PAIR32 = 1, HEXVAL_OPT_PREFETCH = 2 };
 
 typedef struct {
   uint64_t elements;        /* elements processed since the last reset */
@@ -143,8 +145,9 @@ enum {
   HEXVAL_PH_NODES32 = 0, /* FP64 nodes -> FP32 copy (FP32 form, indexed input) */
   HEXVAL_PH_BULK32 = 1,  /* FP32 bulk pass */
   HEXVAL_PH_BULK64 = 2,  /* FP64 bulk pass */
-  HEXVAL_PH_TAIL = 3,    /* FP64 redo of FP32 escalations and refinement */
-  HEXVAL_PH_EXACT = 4,   /* exact tier */
+  HEXVAL_PH_TAIL = 3,    /* FP64 redo of FP32 escalations, refinement and
+                            the exact tier (one launch) */
+  HEXVAL_PH_EXACT = 4,   /* unused: the exact tier runs inside the tail */
   HEXVAL_PH_COUNT = 8
 };
 typedef struct {

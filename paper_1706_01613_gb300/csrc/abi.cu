@@ -105,8 +105,6 @@ int run_batches(hexval_ctx* h, Batch p, int64_t n_hex, cudaStream_t st) {
                          : phase(h, HEXVAL_PH_BULK64, st, [&] { return hexval::launch_bulk64(p, st); });
     if (e == cudaSuccess)
       e = phase(h, HEXVAL_PH_TAIL, st, [&] { return hexval::launch_tail(p, fp32, st); });
-    if (e == cudaSuccess)
-      e = phase(h, HEXVAL_PH_EXACT, st, [&] { return hexval::launch_exact(p, st); });
     if (e != cudaSuccess) {
       // the tail resets the counters; if it could not run, reset them here
       cudaGetLastError();
@@ -142,7 +140,8 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
   if (cfg->max_batch == 0 || cfg->max_batch > (1ull << 31) || cfg->queue_capacity == 0 ||
       cfg->queue_capacity > (1ull << 31) || cfg->exact_capacity == 0 ||
       cfg->exact_capacity > (1ull << 31) || cfg->max_nodes > (1ull << 31) ||
-      (cfg->options & ~static_cast<uint32_t>(HEXVAL_OPT_PAIR32)) || cfg->reserved[0] ||
+      (cfg->options & ~static_cast<uint32_t>(HEXVAL_OPT_PAIR32 | HEXVAL_OPT_PREFETCH)) ||
+      cfg->reserved[0] ||
       cfg->reserved[1] ||
       (cfg->bulk_threads != 0 && cfg->bulk_threads != 64 && cfg->bulk_threads != 128 &&
        cfg->bulk_threads != 256))
@@ -236,6 +235,7 @@ int hexval_check_indexed(hexval_handle h, int64_t n_nodes, const double* nodes, 
   p.conn = conn;
   p.indexed = 1;
   p.pair32 = (h->cfg.options & HEXVAL_OPT_PAIR32) != 0;
+  p.prefetch32 = (h->cfg.options & HEXVAL_OPT_PREFETCH) != 0;
   p.bulk_threads = static_cast<int>(h->cfg.bulk_threads);
   p.flags = flags;
   p.bmin = bmin;

@@ -6,8 +6,9 @@
 //                  signs (element64.cuh).  Undecided elements enter level 0 of
 //                  the refinement queue; uncertifiable ones the exact list.
 //  bulk32_kernel   the same in FP32 with a certified FP32 error bound; only
-//                  clear-cut elements are decided, the rest are appended to
-//                  the escalation list and redone in FP64 by the tail kernel.
+//                  clear-cut elements are decided, the rest are escalated to
+//                  FP64: the first kEscInBulk of a batch right here, by the
+//                  whole warp (warp_items.cuh), the others by the tail kernel.
 //  nodes32_kernel  FP64 nodes -> FP32 on the integer pipe, for the indexed
 //                  FP32 pass (one conversion per node instead of per corner).
 //
@@ -16,13 +17,39 @@
 // and L the largest |component| among them, every sample and coefficient is
 // within 200 eps L^2 + 740 u L^3 of its exact value; the kernel uses
 // 256 eps L^2 + 1024 u L^3 with eps = 2^-23 X + 2^-24 L, X >= |coordinates|.
-#include "element64.cuh"
+#include "warp_items.cuh"
 
 namespace hexval {
 
 namespace {
 
 constexpr int kBulkThreads = 256;
+
+// Escalation of a warp's uncertain elements (all 32 lanes call it; `want`
+// marks this lane's element e).  They are appended to the escalation list;
+// those that land in its first kEscInBulk positions are redone in FP64 here,
+// one at a time by the whole warp, on `sm` (kElemScratch doubles of shared
+// memory per warp); the others are written to the list for the tail kernel.
+__device__ __forceinline__ void escalate(const Batch& p, bool want, unsigned int e, double* sm) {
+  const unsigned int pos = warp_append(&p.s.cnt->esc_count, want);
+  if (want && pos >= kEscInBulk) p.s.esc[pos] = e;  // capacity = batch size
+  unsigned int mine = __ballot_sync(kFull, want && pos < kEscInBulk);
+  while (mine) {
+    const int src = __ffs(mine) - 1;
+    mine &= mine - 1;
+    fp64_element_warp(p, __shfl_sync(kFull, e, src), sm);
+  }
+}
+
+// This warp's part of the dynamic shared memory of a bulk FP32 kernel.
+__device__ __forceinline__ double* warp_scratch() {
+  extern __shared__ double bulk_sm[];
+  return bulk_sm + (threadIdx.x >> 5) * kElemScratch;
+}
+
+inline size_t scratch_bytes(int threads) {
+  return static_cast<size_t>(threads / 32) * kElemScratch * sizeof(double);
+}
 
 __global__ void __launch_bounds__(kBulkThreads) bulk64_kernel(Batch p) {
   unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -60,6 +87,66 @@ __device__ __forceinline__ double f2d_int(float v) {
 
 __device__ __forceinline__ float fabsmax3(float m, const V3<float>& v) {
   return fmaxf(m, fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))));
+}
+
+// The FP32 decision of one element from its 8 nodes (FP32): 0 invalid,
+// 1 valid, 3 escalate to FP64; lo / hi = min / max of the 27 coefficients.
+// X bounds |coordinate| (indexed: |node 1| only, completed here with 3 L).
+template <bool INDEXED>
+__device__ __forceinline__ int fp32_decide(const V3<float> Y[8], float X, bool bad, float& lo,
+                                           float& hi) {
+  int outcome;
+  V3<float> a[4], b[4], gg[4];
+  edges_from_nodes(Y, a, b, gg);
+  float L = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    L = fabsmax3(L, a[q]);
+    L = fabsmax3(L, b[q]);
+    L = fabsmax3(L, gg[q]);
+  }
+  if (INDEXED) X = fmaf(3.f, L, X);  // every node is within 3 edges of node 1
+  float eps = fmaf(0x1p-24f, L, 0x1p-23f * X);
+  float L2 = L * L;
+  float E = fmaf(256.f * eps, L2, 1024.f * 0x1p-24f * (L2 * L)) * 1.0001f;
+  // too small (underflow) or too large (overflow) for the FP32 bound
+  bad |= !(L >= 0x1p-30f) || !(E < 0x1p100f);
+  if (bad) {
+    outcome = 3;
+  } else {
+    Scaled<float> s;
+    coefficients_from_edges(a, b, gg, s);
+    // per-class minima / maxima (scales 1, 4, 2, 4, 8)
+    float mnC = s.corner[0], mxC = s.corner[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+      mnC = fminf(mnC, s.corner[k]);
+      mxC = fmaxf(mxC, s.corner[k]);
+    }
+    float mnS = s.edgeC[0];
+#pragma unroll
+    for (int e = 1; e < 12; ++e) mnS = fminf(mnS, s.edgeC[e]);
+    float mnE = s.edge[0], mxE = s.edge[0];
+#pragma unroll
+    for (int e = 1; e < 12; ++e) {
+      mnE = fminf(mnE, s.edge[e]);
+      mxE = fmaxf(mxE, s.edge[e]);
+    }
+    float mnF = s.face[0], mxF = s.face[0];
+#pragma unroll
+    for (int f = 1; f < 6; ++f) {
+      mnF = fminf(mnF, s.face[f]);
+      mxF = fmaxf(mxF, s.face[f]);
+    }
+    // Step 2: a sample certainly <= 0; Step 4: all 27 certainly > 0
+    bool invalid = (mnC <= -E) | (mnS <= -4.f * E);
+    bool valid = (mnC > E) & (mnS > 4.f * E) & (mnE > 2.f * E) & (mnF > 4.f * E) &
+                 (s.centre > 8.f * E);
+    outcome = invalid ? 0 : (valid ? 1 : 3);
+    lo = fminf(fminf(mnC, mnE * 0.5f), fminf(mnF * 0.25f, s.centre * 0.125f));
+    hi = fmaxf(fmaxf(mxC, mxE * 0.5f), fmaxf(mxF * 0.25f, s.centre * 0.125f));
+  }
+  return outcome;
 }
 
 // Decides what FP32 can decide; everything else is escalated to FP64.
@@ -107,66 +194,11 @@ __global__ void __launch_bounds__(kBulkThreads) bulk32_kernel(Batch p) {
         X = fabsmax3(0.f, Y[0]);  // completed below with 3 L
       }
     }
-    if (outcome < 0) {
-      V3<float> a[4], b[4], gg[4];
-      edges_from_nodes(Y, a, b, gg);
-      float L = 0.f;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        L = fabsmax3(L, a[q]);
-        L = fabsmax3(L, b[q]);
-        L = fabsmax3(L, gg[q]);
-      }
-      if (INDEXED) X = fmaf(3.f, L, X);  // every node is within 3 edges of node 1
-      float eps = fmaf(0x1p-24f, L, 0x1p-23f * X);
-      float L2 = L * L;
-      float E = fmaf(256.f * eps, L2, 1024.f * 0x1p-24f * (L2 * L)) * 1.0001f;
-      // too small (underflow) or too large (overflow) for the FP32 bound
-      bad |= !(L >= 0x1p-30f) || !(E < 0x1p100f);
-      if (bad) {
-        outcome = 3;
-      } else {
-        Scaled<float> s;
-        coefficients_from_edges(a, b, gg, s);
-        // per-class minima / maxima (scales 1, 4, 2, 4, 8)
-        float mnC = s.corner[0], mxC = s.corner[0];
-#pragma unroll
-        for (int k = 1; k < 8; ++k) {
-          mnC = fminf(mnC, s.corner[k]);
-          mxC = fmaxf(mxC, s.corner[k]);
-        }
-        float mnS = s.edgeC[0];
-#pragma unroll
-        for (int e = 1; e < 12; ++e) mnS = fminf(mnS, s.edgeC[e]);
-        float mnE = s.edge[0], mxE = s.edge[0];
-#pragma unroll
-        for (int e = 1; e < 12; ++e) {
-          mnE = fminf(mnE, s.edge[e]);
-          mxE = fmaxf(mxE, s.edge[e]);
-        }
-        float mnF = s.face[0], mxF = s.face[0];
-#pragma unroll
-        for (int f = 1; f < 6; ++f) {
-          mnF = fminf(mnF, s.face[f]);
-          mxF = fmaxf(mxF, s.face[f]);
-        }
-        // Step 2: a sample certainly <= 0; Step 4: all 27 certainly > 0
-        bool invalid = (mnC <= -E) | (mnS <= -4.f * E);
-        bool valid = (mnC > E) & (mnS > 4.f * E) & (mnE > 2.f * E) & (mnF > 4.f * E) &
-                     (s.centre > 8.f * E);
-        outcome = invalid ? 0 : (valid ? 1 : 3);
-        lo = fminf(fminf(mnC, mnE * 0.5f), fminf(mnF * 0.25f, s.centre * 0.125f));
-        hi = fmaxf(fmaxf(mxC, mxE * 0.5f), fmaxf(mxF * 0.25f, s.centre * 0.125f));
-      }
-    }
+    if (outcome < 0) outcome = fp32_decide<INDEXED>(Y, X, bad, lo, hi);
   }
-  bool want_e = act && outcome == 3;
-  unsigned int pos = warp_append(&S.cnt->esc_count, want_e);
-  if (!act) return;
-  if (want_e) {
-    S.esc[pos] = i;  // capacity = batch size: cannot overflow
-    return;
-  }
+  const bool want_e = act && outcome == 3;
+  escalate(p, want_e, i, warp_scratch());
+  if (!act || want_e) return;
   if (outcome == 5) {
     p.flags[g] = make_flag(kVUndecided, 0, 0);
     set_status(S.status, kSbIndex);
@@ -178,6 +210,83 @@ __global__ void __launch_bounds__(kBulkThreads) bulk32_kernel(Batch p) {
   p.flags[g] = make_flag(outcome == 0 ? kVInvalid : kVValid, 0, 0);
   if (p.bmin) p.bmin[g] = f2d_int(lo);
   if (p.bmax) p.bmax[g] = f2d_int(hi);
+}
+
+// Indexed FP32 pass on a persistent grid: each thread walks elements i,
+// i + stride, ... and loads the connectivity of its next element before it
+// works on the current one, so that only the node loads (L2) are exposed.
+__global__ void __launch_bounds__(kBulkThreads) bulk32p_kernel(Batch p) {
+  const Scratch& S = p.s;
+  const unsigned int n = static_cast<unsigned int>(p.n);
+  const unsigned int stride = gridDim.x * blockDim.x;
+  unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int4 c0 = make_int4(0, 0, 0, 0), c1 = c0;
+  if (i < n) {
+    const int4* c4 = reinterpret_cast<const int4*>(p.conn + 8 * (p.base + i));
+    c0 = __ldg(c4);
+    c1 = __ldg(c4 + 1);
+  }
+  for (unsigned int base = blockIdx.x * blockDim.x; base < n; base += stride, i += stride) {
+    const bool act = i < n;
+    const int id[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    if (i + stride < n) {  // next element's connectivity
+      const int4* c4 = reinterpret_cast<const int4*>(p.conn + 8 * (p.base + i + stride));
+      c0 = __ldg(c4);
+      c1 = __ldg(c4 + 1);
+    }
+    const int64_t g = p.base + i;
+    int outcome = -1;
+    float lo = 0.f, hi = 0.f;
+    if (act) {
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        ok &= static_cast<uint32_t>(id[k]) < static_cast<uint64_t>(p.n_nodes);
+      if (!ok) {
+        outcome = 5;
+      } else {
+        const float4* N = reinterpret_cast<const float4*>(S.node32);
+        V3<float> Y[8];
+        float badw = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          float4 h = __ldg(N + id[k]);
+          Y[k] = {h.x, h.y, h.z};
+          badw += h.w;
+        }
+        outcome = fp32_decide<true>(Y, fabsmax3(0.f, Y[0]), badw != 0.f, lo, hi);
+      }
+    }
+    const bool want_e = act && outcome == 3;
+    escalate(p, want_e, i, warp_scratch());
+    if (act && !want_e) {
+      if (outcome == 5) {
+        p.flags[g] = make_flag(kVUndecided, 0, 0);
+        set_status(S.status, kSbIndex);
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        if (p.bmin) p.bmin[g] = nan;
+        if (p.bmax) p.bmax[g] = nan;
+      } else {
+        p.flags[g] = make_flag(outcome == 0 ? kVInvalid : kVValid, 0, 0);
+        if (p.bmin) p.bmin[g] = f2d_int(lo);
+        if (p.bmax) p.bmax[g] = f2d_int(hi);
+      }
+    }
+  }
+}
+
+int bulk32p_blocks(int threads) {
+  static int cached_threads = -1, blocks = 0;
+  if (threads != cached_threads) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bulk32p_kernel, threads,
+                                                  scratch_bytes(threads));
+    blocks = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    cached_threads = threads;
+  }
+  return blocks;
 }
 
 // Per-lane decision of the FP32 pass from the scaled coefficients of one
@@ -326,9 +435,8 @@ __global__ void __launch_bounds__(kPairThreads) bulk32x2_kernel(Batch p) {
     if (out1 < 0) out1 = bad1 ? 3 : r1;
   }
   const bool e0 = act0 && out0 == 3, e1 = act1 && out1 == 3;
-  // two appends per thread, each warp-aggregated
-  unsigned int pos0 = warp_append(&S.cnt->esc_count, e0);
-  unsigned int pos1 = warp_append(&S.cnt->esc_count, e1);
+  escalate(p, e0, i0, warp_scratch());
+  escalate(p, e1, i1, warp_scratch());
   if (!act0) return;
   const double nan = __longlong_as_double(0x7ff8000000000000LL);
   uint8_t f0 = 0, f1 = 0;
@@ -346,8 +454,6 @@ __global__ void __launch_bounds__(kPairThreads) bulk32x2_kernel(Batch p) {
   };
   fin(out0, lo0, hi0, f0, l0, h0);
   if (act1) fin(out1, lo1, hi1, f1, l1, h1);
-  if (e0) S.esc[pos0] = i0;
-  if (e1) S.esc[pos1] = i1;
   const int64_t g0 = p.base + i0;
   if (act1 && !e0 && !e1 && (g0 & 1) == 0) {  // both written: paired stores
     *reinterpret_cast<uchar2*>(p.flags + g0) = make_uchar2(f0, f1);
@@ -419,17 +525,24 @@ cudaError_t launch_bulk32(const Batch& p, cudaStream_t st) {
     int64_t threads = (p.n + 1) / 2;
     unsigned int blocks = static_cast<unsigned int>((threads + bt - 1) / bt);
     if (p.indexed)
-      bulk32x2_kernel<true><<<blocks, bt, 0, st>>>(p);
+      bulk32x2_kernel<true><<<blocks, bt, scratch_bytes(bt), st>>>(p);
     else
-      bulk32x2_kernel<false><<<blocks, bt, 0, st>>>(p);
+      bulk32x2_kernel<false><<<blocks, bt, scratch_bytes(bt), st>>>(p);
     return cudaGetLastError();
   }
   const int bt = p.bulk_threads ? p.bulk_threads : kBulkThreads;
+  if (p.indexed && p.prefetch32) {
+    int64_t need = (p.n + bt - 1) / bt;
+    int64_t blocks = bulk32p_blocks(bt);
+    bulk32p_kernel<<<static_cast<unsigned int>(need < blocks ? need : blocks), bt,
+                     scratch_bytes(bt), st>>>(p);
+    return cudaGetLastError();
+  }
   unsigned int blocks = static_cast<unsigned int>((p.n + bt - 1) / bt);
   if (p.indexed)
-    bulk32_kernel<true><<<blocks, bt, 0, st>>>(p);
+    bulk32_kernel<true><<<blocks, bt, scratch_bytes(bt), st>>>(p);
   else
-    bulk32_kernel<false><<<blocks, bt, 0, st>>>(p);
+    bulk32_kernel<false><<<blocks, bt, scratch_bytes(bt), st>>>(p);
   return cudaGetLastError();
 }
 

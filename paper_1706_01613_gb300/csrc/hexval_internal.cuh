@@ -42,17 +42,25 @@ constexpr uint32_t kSbRange = 8u;
 
 constexpr int kMaxDepth = 15;
 
-// Per-batch counters.  They are zero when a batch starts: the last block of
-// the tail kernel resets them once every block is done with them (and the
-// handle creation zeroes them once).
+// Per-batch counters.  They are zero when a batch starts: the tail kernel,
+// which ends every batch, resets them once every block is done with them
+// (and the handle creation zeroes them once).
 struct Counters {
   unsigned int level_count[kMaxDepth + 2];  // boxes queued per level; [0] = refined elements
-  unsigned int esc_count;                   // FP32 -> FP64 escalation list
+  unsigned int esc_count;                   // FP32 -> FP64 escalations (list + in-pass)
   unsigned int exact_count;                 // exact-tier list
   unsigned int arrive;                      // grid barrier of the tail kernel
   unsigned int done;                        // blocks of the tail kernel that finished
-  unsigned int pad[11];
+  unsigned int amb_count;                   // boxes that sent their element to the exact tier
+  unsigned int pad[10];
 };
+
+// Escalations of the FP32 pass: the first kEscInBulk elements appended to
+// the escalation list of a batch are redone in FP64 by the FP32 pass itself
+// (one element at a time by a whole warp, on the FP64 unit that the FP32
+// pass leaves idle); their list entries stay unwritten.  Entries from
+// kEscInBulk on are written and redone by the tail kernel.
+constexpr unsigned int kEscInBulk = 4096;
 
 // Counters accumulated across calls (hexval_get_stats).
 struct Stats {
@@ -99,6 +107,7 @@ struct Batch {
   int indexed;
   int pair32;        // FP32 pass: two elements per thread with packed f32x2 math
   int bulk_threads;  // block size of the bulk kernels (0: default)
+  int prefetch32;    // indexed FP32 pass on a persistent grid with prefetch
   // outputs (indexed by base + e)
   uint8_t* flags;
   double* bmin;
@@ -436,10 +445,11 @@ __device__ __forceinline__ T ldcg(const T* p) {
 }
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident), with
-// a bounded wait: after kSpinLimit polls the block records kSbTimeout and
-// goes on (results of that call are then reported as unreliable by the
-// status, and the kernel still terminates).
-constexpr long long kSpinLimit = 1ll << 26;
+// a bounded wait: after kSpinLimit polls (each an L2 round trip, well over a
+// second in all) the block records kSbTimeout and goes on (results of that
+// call are then reported as unreliable by the status, and the kernel still
+// terminates).
+constexpr long long kSpinLimit = 1ll << 24;
 __device__ __forceinline__ void grid_barrier(unsigned int* arrive, unsigned int& epoch,
                                              uint32_t* status) {
   __syncthreads();
@@ -454,7 +464,6 @@ __device__ __forceinline__ void grid_barrier(unsigned int* arrive, unsigned int&
         atomicOr(status, kSbTimeout);
         break;
       }
-      __nanosleep(100);
     }
     __threadfence();
   }
@@ -515,7 +524,6 @@ cudaError_t launch_bulk64(const Batch& p, cudaStream_t st);
 cudaError_t launch_bulk32(const Batch& p, cudaStream_t st);
 cudaError_t launch_nodes32(const Batch& p, cudaStream_t st);
 cudaError_t launch_tail(const Batch& p, bool from_list, cudaStream_t st);
-cudaError_t launch_exact(const Batch& p, cudaStream_t st);
 uint64_t exact_work_words();
 
 }  // namespace hexval

@@ -5,7 +5,7 @@
 // or in a process whose allocator is locked after start-up).
 //
 // It launches the same kernels as hexval_check_soa with a FP64 handle
-// (bulk64, tail, exact), but their scratch -- refinement queue, per-element
+// (bulk64, then the tail with the exact tier), but their scratch -- refinement queue, per-element
 // refinement state, exact-tier list and stacks, counters, statistics and
 // status -- lives in one file-scope static device array of fixed size,
 // instead of memory allocated by hexval_create.  The caller passes only the
@@ -128,8 +128,7 @@ extern "C" int hexval_check_soa_noalloc(int64_t n_hex, const double* corners, ui
     s.stats = reinterpret_cast<hexval::Stats*>(base + kOffStats);
     s.status = reinterpret_cast<uint32_t*>(base + kOffStatus);
     if (hexval::launch_bulk64(p, st) != cudaSuccess ||
-        hexval::launch_tail(p, false, st) != cudaSuccess ||
-        hexval::launch_exact(p, st) != cudaSuccess) {
+        hexval::launch_tail(p, false, st) != cudaSuccess) {
       cudaGetLastError();
       cudaMemsetAsync(base + kOffCnt, 0, sizeof(hexval::Counters), st);
       return HEXVAL_E_CUDA;

@@ -1,18 +1,16 @@
-// Everything after the bulk pass, in two launches.
-//
-// tail_kernel, one persistent cooperative launch:
-//  phase E  (FP32 form) the elements escalated by the FP32 bulk pass are
-//           redone in FP64 (element64.cuh);
+// Everything after the bulk pass, in one persistent cooperative launch:
+//  phase E  (FP32 form) the escalated elements that the FP32 pass left in
+//           the escalation list are redone in FP64 (element64.cuh);
 //  levels   refinement of undecided elements (Sec. 6, recursive_subdivision),
 //           breadth first, one level per grid-wide step;
-//  phase F  verdicts of the refined elements.
-// Grid-wide steps are separated by a bounded grid barrier.  Every box count
-// is read after a barrier, so all blocks take the same branches; with
-// nothing to refine the kernel returns at its first instructions.
-//
-// exact_kernel: the exact tier (exact.cuh) for elements whose signs could
-// not be certified; its last block folds the batch counters into the
-// statistics and resets them for the next batch.
+//  phase F  verdicts of the refined elements;
+//  phase X  the exact tier (exact.cuh) for elements whose signs could not be
+//           certified, only when some element needs it.
+// Grid-wide steps are separated by a bounded grid barrier.  Every count that
+// decides a branch is read after a barrier (or was written by an earlier
+// launch), so all blocks take the same branches; with nothing to do the
+// kernel returns at its first instructions.  The last block to finish folds
+// the batch counters into the statistics and resets them.
 //
 // Refinement.  Level d holds boxes of depth d whose corners are certainly
 // positive and which are certainly not certified.  Each is split at 1/2
@@ -173,6 +171,7 @@ __device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool ac
   }
   if (act) {
     if (bits) atomicOr(&S.slot_state[slot], bits);
+    if (bits & (kStAmbig | kStOverflow)) atomicAdd(&S.cnt->amb_count, 1u);
     if (bits & kStOverflow) set_status(S.status, kSbQueue);
     S.slot_lev[slot] = static_cast<uint32_t>(child_level);
   }
@@ -227,26 +226,57 @@ constexpr unsigned int kWarpItemsMax = 8;
   for (unsigned int i = blockIdx.x + gridDim.x * (threadIdx.x >> 5); i < (n);      \
        i += gridDim.x * (blockDim.x >> 5))
 
+// Folds the batch counters into the statistics and resets them (one thread,
+// once every block of the batch's last kernel is done with the counters).
+__device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned int nx) {
+  const Scratch& S = p.s;
+  Counters* C = S.cnt;
+  __threadfence();
+  Stats* st = S.stats;
+  unsigned long long boxes = 0, mx = 0;
+  for (int l = 1; l <= kMaxDepth + 1; ++l) {
+    unsigned long long c = ldcg(&C->level_count[l]);
+    boxes += c;
+    mx = c > mx ? c : mx;
+  }
+  atomicAdd(&st->elements, static_cast<unsigned long long>(p.n));
+  atomicAdd(&st->escalated_fp64, static_cast<unsigned long long>(ldcg(&C->esc_count)));
+  atomicAdd(&st->refined, static_cast<unsigned long long>(ldcg(&C->level_count[0])));
+  atomicAdd(&st->boxes, boxes);
+  atomicAdd(&st->exact, static_cast<unsigned long long>(nx));
+  atomicMax(&st->max_level_boxes, mx);
+  unsigned int* w = reinterpret_cast<unsigned int*>(C);
+  for (unsigned int k = 0; k < sizeof(Counters) / sizeof(unsigned int); ++k) w[k] = 0u;
+  __threadfence();
+}
+
 __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from_list) {
   const Scratch& S = p.s;
   Counters* C = S.cnt;
-  const unsigned int n_esc = from_list ? ldcg(&C->esc_count) : 0u;
-  if (n_esc == 0 && ldcg(&C->level_count[0]) == 0) return;  // nothing to refine
+  // escalation list entries [kEscInBulk, n_list) are left for this kernel
+  const unsigned int n_list = from_list ? ldcg(&C->esc_count) : 0u;
+  const unsigned int n_esc = n_list > kEscInBulk ? n_list - kEscInBulk : 0u;
+  if (n_esc == 0 && ldcg(&C->level_count[0]) == 0 && ldcg(&C->exact_count) == 0) {
+    // nothing left: every block reads only counters that are, or become,
+    // zero here, so block 0 may end the batch at once
+    if (blockIdx.x == 0 && threadIdx.x == 0) fold_stats_and_reset(p, 0u);
+    return;
+  }
   __shared__ double wsm[kTailThreads / 32][kWarpScratch];
   double* mysm = wsm[threadIdx.x >> 5];
   const unsigned int warp_items = kWarpItemsMax * gridDim.x * (blockDim.x >> 5);
   unsigned int epoch = 0;
   if (n_esc) {  // phase E
+    const uint32_t* esc = S.esc + kEscInBulk;
     if (n_esc <= warp_items) {
-      FOR_EACH_WARP_ITEM(n_esc, i) fp64_element_warp(p, ldcg(S.esc + i), mysm);
+      FOR_EACH_WARP_ITEM(n_esc, i) fp64_element_warp(p, ldcg(esc + i), mysm);
     } else {
-      FOR_EACH_ITEM(n_esc, i, act) fp64_item(p, act, act ? ldcg(S.esc + i) : 0u);
+      FOR_EACH_ITEM(n_esc, i, act) fp64_item(p, act, act ? ldcg(esc + i) : 0u);
     }
     grid_barrier(&C->arrive, epoch, S.status);
   }
   const unsigned int n0 = min(ldcg(&C->level_count[0]), static_cast<unsigned int>(S.qcap));
-  if (n0 == 0) return;
-  for (int level = 0; level < p.max_depth; ++level) {
+  for (int level = 0; n0 && level < p.max_depth; ++level) {
     const unsigned int n = min(ldcg(&C->level_count[level]),
                                static_cast<unsigned int>(S.qcap));
     if (n == 0) break;
@@ -257,44 +287,28 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
     }
     grid_barrier(&C->arrive, epoch, S.status);
   }
-  FOR_EACH_ITEM(n0, i, act) finalize_slot(p, act, i);
-}
-
-// Exact tier over the list, then (last block) statistics and the reset of
-// the batch counters for the next batch.
-constexpr int kExactThreads = 64;
-constexpr int kExactBlocks = exact_tier::kWorkers / kExactThreads;
-
-__global__ void __launch_bounds__(kExactThreads) exact_kernel(Batch p) {
-  const Scratch& S = p.s;
-  Counters* C = S.cnt;
-  const unsigned int nx = min(ldcg(&C->exact_count), static_cast<unsigned int>(S.exact_cap));
-  const unsigned int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  for (unsigned int i = tid; i < nx; i += exact_tier::kWorkers)
-    exact_tier::exact_element(p, ldcg(S.exact_list + i), tid);
+  // Elements for the exact tier: those already listed, and those whose boxes
+  // met an uncertain sign or a full queue (listed by phase F below).
+  const bool exact = ldcg(&C->exact_count) != 0u || ldcg(&C->amb_count) != 0u;
+  if (n0) {  // phase F
+    FOR_EACH_ITEM(n0, i, act) finalize_slot(p, act, i);
+    if (exact) grid_barrier(&C->arrive, epoch, S.status);
+  }
+  unsigned int nx = 0;
+  if (exact) {  // phase X: lane 0 of the first kWorkers warps, one element at a time each
+    nx = min(ldcg(&C->exact_count), static_cast<unsigned int>(S.exact_cap));
+    const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
+    if ((threadIdx.x & 31u) == 0u)
+      for (unsigned int w = blockIdx.x + gridDim.x * (threadIdx.x >> 5); w < exact_tier::kWorkers;
+           w += nwarps)
+        for (unsigned int i = w; i < nx; i += exact_tier::kWorkers)
+          exact_tier::exact_element(p, ldcg(S.exact_list + i), w);
+  }
+  // the last block ends the batch
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    unsigned int done = atomicAdd(&C->done, 1u);
-    if (done == gridDim.x - 1) {
-      __threadfence();
-      Stats* st = S.stats;
-      unsigned long long boxes = 0, mx = 0;
-      for (int l = 1; l <= kMaxDepth + 1; ++l) {
-        unsigned long long c = ldcg(&C->level_count[l]);
-        boxes += c;
-        mx = c > mx ? c : mx;
-      }
-      atomicAdd(&st->elements, static_cast<unsigned long long>(p.n));
-      atomicAdd(&st->escalated_fp64, static_cast<unsigned long long>(ldcg(&C->esc_count)));
-      atomicAdd(&st->refined, static_cast<unsigned long long>(ldcg(&C->level_count[0])));
-      atomicAdd(&st->boxes, boxes);
-      atomicAdd(&st->exact, static_cast<unsigned long long>(nx));
-      atomicMax(&st->max_level_boxes, mx);
-      unsigned int* w = reinterpret_cast<unsigned int*>(C);
-      for (unsigned int k = 0; k < sizeof(Counters) / sizeof(unsigned int); ++k) w[k] = 0u;
-      __threadfence();
-    }
+    if (atomicAdd(&C->done, 1u) == gridDim.x - 1) fold_stats_and_reset(p, nx);
   }
 }
 
@@ -322,11 +336,6 @@ cudaError_t launch_tail(const Batch& p, bool from_list, cudaStream_t st) {
   void* args[] = {&arg, &fl};
   return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(tail_kernel), dim3(tail_blocks()),
                                      dim3(kTailThreads), args, 0, st);
-}
-
-cudaError_t launch_exact(const Batch& p, cudaStream_t st) {
-  exact_kernel<<<kExactBlocks, kExactThreads, 0, st>>>(p);
-  return cudaGetLastError();
 }
 
 }  // namespace hexval

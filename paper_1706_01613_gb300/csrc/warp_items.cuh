@@ -19,6 +19,7 @@
 namespace hexval {
 
 constexpr int kWarpScratch = 272;  // doubles per warp (box: 27 + 45 + 75 + 125)
+constexpr int kElemScratch = 116;  // doubles per warp used by fp64_element_warp
 constexpr unsigned int kFull = 0xffffffffu;
 
 __device__ __forceinline__ double shfl_d(double v, int src) {
@@ -84,7 +85,7 @@ __device__ __forceinline__ void sample_columns(int t, int& A, int& B, int& C) {
 
 // Warp-cooperative fp64_element (element64.cuh): element e of the batch,
 // all 32 lanes, `sm` = this warp's shared scratch.
-__device__ __noinline__ void fp64_element_warp(const Batch& p, uint32_t e, double* sm) {
+static __device__ __noinline__ void fp64_element_warp(const Batch& p, uint32_t e, double* sm) {
   const Scratch& S = p.s;
   const int lane = threadIdx.x & 31;
   const int64_t g = p.base + e;
@@ -274,7 +275,7 @@ __device__ __forceinline__ void split5_row(const double* in, int stride_in, doub
 }
 
 // Warp-cooperative refine_box: box `idx` of level `level`, all 32 lanes.
-__device__ __noinline__ void refine_box_warp(const Batch& p, int level, unsigned int idx,
+static __device__ __noinline__ void refine_box_warp(const Batch& p, int level, unsigned int idx,
                                              double* sm) {
   const Scratch& S = p.s;
   const int lane = threadIdx.x & 31;
@@ -356,6 +357,7 @@ __device__ __noinline__ void refine_box_warp(const Batch& p, int level, unsigned
   }
   if (lane == 0) {
     if (bits) atomicOr(&S.slot_state[slot], bits);
+    if (bits & (kStAmbig | kStOverflow)) atomicAdd(&S.cnt->amb_count, 1u);
     if (bits & kStOverflow) set_status(S.status, kSbQueue);
     S.slot_lev[slot] = static_cast<uint32_t>(child_level);
   }

@@ -20,7 +20,8 @@ CODES = {0: "HEXVAL_OK", -1: "HEXVAL_E_ARG", -2: "HEXVAL_E_NOMEM", -3: "HEXVAL_E
          -4: "HEXVAL_E_INDEX", -5: "HEXVAL_E_QUEUE", -6: "HEXVAL_E_TIMEOUT",
          -7: "HEXVAL_E_RANGE"}
 FP64, FP32_FILTERED = 0, 1
-OPT_PAIR32 = 1  # hexval_config.options: packed f32x2 FP32 bulk pass
+OPT_PAIR32 = 1    # hexval_config.options: packed f32x2 FP32 bulk pass
+OPT_PREFETCH = 2  # hexval_config.options: persistent indexed FP32 pass with prefetch
 VALID, INVALID, UNDECIDED, NONFINITE = 1, 2, 3, 4
 
 # every function declared in include/hexval.h (the CPU test checks the list)

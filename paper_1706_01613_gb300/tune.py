@@ -25,8 +25,10 @@ def candidates(precision):
     out = []
     for bt in (64, 128, 256):
         out.append(dict(options=0, bulk_threads=bt))
-        if precision == "fp32" and bt <= 128:
-            out.append(dict(options=hv.OPT_PAIR32, bulk_threads=bt))
+        if precision == "fp32":
+            out.append(dict(options=hv.OPT_PREFETCH, bulk_threads=bt))
+            if bt <= 128:
+                out.append(dict(options=hv.OPT_PAIR32, bulk_threads=bt))
     return out
 
 

@@ -288,27 +288,28 @@ def test_full_affine_mixture_sampled(prec):
 
 
 @pytest.mark.parametrize("kind", ["soa", "indexed"])
-def test_scalar_and_packed_fp32_agree(kind):
-    """The FP32 pass with one element per thread (scalar) and with two per
-    thread (packed f32x2) give identical flags and coefficients, and both
-    match the oracle; odd sizes exercise the idle second lane."""
-    a = hv.Validator(precision="fp32", max_depth=8, **CAPS)
-    b = hv.Validator(precision="fp32", max_depth=8, options=hv.OPT_PAIR32, **CAPS)
+def test_fp32_variants_agree(kind):
+    """The FP32 pass with one element per thread (scalar), two per thread
+    (packed f32x2) and on a persistent prefetching grid give identical flags
+    and coefficients that match the oracle; odd sizes exercise the idle
+    second lane."""
+    vs = [hv.Validator(precision="fp32", max_depth=8, options=o, **CAPS)
+          for o in (0, hv.OPT_PAIR32, hv.OPT_PREFETCH)]
     if kind == "soa":
         X = synth.perturbed_cubes(20_001, noise=0.45, seed=77)
-        ga, gb = _run_soa(a, X), _run_soa(b, X)
+        got = [_run_soa(v, X)[:3] for v in vs]
         want = oracle.check_soa(X, max_depth=8)
     else:
         nodes, conn = synth.structured_grid(31, 17, 13, sigma=0.3, seed=78)
         N, C = torch.from_numpy(nodes).cuda(), torch.from_numpy(conn).cuda()
-        ga = [t.cpu().numpy() for t in a.check_indexed(N, C)]
-        gb = [t.cpu().numpy() for t in b.check_indexed(N, C)]
+        got = [[t.cpu().numpy() for t in v.check_indexed(N, C)] for v in vs]
         want = oracle.check_indexed(nodes, conn, max_depth=8)
-    for x, y in zip(ga[:3], gb[:3]):
-        assert np.array_equal(x, y, equal_nan=True)
-    _compare("fp32", gb[:3], want)
-    a.close()
-    b.close()
+    for other in got[1:]:
+        for x, y in zip(got[0], other):
+            assert np.array_equal(x, y, equal_nan=True)
+    _compare("fp32", got[0], want)
+    for v in vs:
+        v.close()
 
 
 def test_autotuner_picks_a_candidate_and_stays_exact(tmp_path):
