@@ -76,7 +76,7 @@ typedef struct {
   uint64_t exact_capacity; /* elements per batch for the exact tier (default 2^16) */
   uint32_t options;        /* HEXVAL_OPT_* bits (default 0) */
   uint32_t bulk_threads;   /* threads per block of the bulk kernels: 0 (default: 256
-                              scalar, 128 packed), 64, 128 or 256 */
+                              for FP64, 128 for FP32), 64, 128 or 256 */
   uint32_t reserved[2];    /* must be 0 */
 } hexval_config;
 
@@ -84,8 +84,10 @@ typedef struct {
  *  HEXVAL_OPT_PAIR32   the FP32 bulk pass with two elements per thread in
  *                      packed f32x2 arithmetic instead of one per thread;
  *  HEXVAL_OPT_PREFETCH the indexed FP32 bulk pass on a persistent grid that
- *                      loads each thread's next connectivity row ahead
- *                      (ignored with HEXVAL_OPT_PAIR32). */
+ *                      stages its inputs through shared memory with
+ *                      asynchronous copies: connectivity two tiles ahead,
+ *                      node records one tile ahead (ignored with
+ *                      HEXVAL_OPT_PAIR32). */
 enum { HEXVAL_OPT_PAIR32 = 1, HEXVAL_OPT_PREFETCH = 2 };
 
 typedef struct {

@@ -23,7 +23,9 @@ namespace hexval {
 
 namespace {
 
-constexpr int kBulkThreads = 256;
+constexpr int kBulkThreads = 256;    // largest block of the bulk kernels
+constexpr int kBulk32Default = 128;  // default block of the FP32 kernels (measured best
+                                     // with 64 on the 128^3 mesh, within noise of 128)
 
 // Escalation of a warp's uncertain elements (all 32 lanes call it; `want`
 // marks this lane's element e).  They are appended to the escalation list;
@@ -212,54 +214,100 @@ __global__ void __launch_bounds__(kBulkThreads) bulk32_kernel(Batch p) {
   if (p.bmax) p.bmax[g] = f2d_int(hi);
 }
 
-// Indexed FP32 pass on a persistent grid: each thread walks elements i,
-// i + stride, ... and loads the connectivity of its next element before it
-// works on the current one, so that only the node loads (L2) are exposed.
-__global__ void __launch_bounds__(kBulkThreads) bulk32p_kernel(Batch p) {
+// Indexed FP32 pass on a persistent grid with its inputs staged through
+// shared memory by asynchronous copies.  Block b works on tiles b, b + G,
+// b + 2G, ... (G blocks, one element per thread and tile).  At the start of
+// tile j a thread takes the node records of its element of tile j and the
+// connectivity row of its element of tile j+1 out of shared memory into
+// registers, then starts the copies of the connectivity of tile j+2 and of
+// the node records of tile j+1 into the same places, and works on tile j
+// while they are in flight: neither the HBM latency of the connectivity nor
+// the L2 latency of the gathered node records is exposed.  Each thread
+// stages only its own element's data, so no block barrier is needed.
+// Shared memory per block of T threads (W warps):
+//   node records  float4 [W][8 nodes][32 lanes]      128 T bytes
+//   connectivity  int4   [2 halves][T]                 32 T bytes
+//   FP64 scratch  double [W][kElemScratch]            (escalations)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned int s = static_cast<unsigned int>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+inline size_t staged_bytes(int threads) {
+  return static_cast<size_t>(threads) * 160 + scratch_bytes(threads);
+}
+
+__global__ void __launch_bounds__(kBulkThreads, 4) bulk32s_kernel(Batch p) {
+  extern __shared__ float4 stage[];
   const Scratch& S = p.s;
-  const unsigned int n = static_cast<unsigned int>(p.n);
-  const unsigned int stride = gridDim.x * blockDim.x;
-  unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int4 c0 = make_int4(0, 0, 0, 0), c1 = c0;
-  if (i < n) {
-    const int4* c4 = reinterpret_cast<const int4*>(p.conn + 8 * (p.base + i));
-    c0 = __ldg(c4);
-    c1 = __ldg(c4 + 1);
-  }
-  for (unsigned int base = blockIdx.x * blockDim.x; base < n; base += stride, i += stride) {
-    const bool act = i < n;
-    const int id[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-    if (i + stride < n) {  // next element's connectivity
-      const int4* c4 = reinterpret_cast<const int4*>(p.conn + 8 * (p.base + i + stride));
-      c0 = __ldg(c4);
-      c1 = __ldg(c4 + 1);
+  const unsigned int T = blockDim.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  float4* const my_nodes = stage + w * 256u + lane;                            // record k: [32 k]
+  int4* const my_conn = reinterpret_cast<int4*>(stage + 8u * T) + threadIdx.x;  // half h: [h T]
+  double* const wsc = reinterpret_cast<double*>(stage + 10u * T) + w * kElemScratch;
+  const float4* const N = reinterpret_cast<const float4*>(S.node32);
+  const unsigned int n = static_cast<unsigned int>(p.n);  // a batch holds < 2^31 elements
+  const unsigned int tiles = (n + T - 1) / T;
+  if (blockIdx.x >= tiles) return;
+  const unsigned int my_tiles = (tiles - 1 - blockIdx.x) / gridDim.x + 1;
+  const unsigned int step = gridDim.x * T;
+  auto issue_conn = [&](unsigned int e) {
+    if (e < n) {
+      const int* src = p.conn + 8 * (p.base + static_cast<int64_t>(e));
+      cp_async16(my_conn, src);
+      cp_async16(my_conn + T, src + 4);
     }
-    const int64_t g = p.base + i;
+  };
+  // node records of element e from its connectivity (in registers); false
+  // if an entry is out of range (nothing is copied then)
+  auto issue_nodes = [&](unsigned int e, const int4& c0, const int4& c1) {
+    const int id[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      ok &= static_cast<uint32_t>(id[k]) < static_cast<uint64_t>(p.n_nodes);
+    if (ok && e < n) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) cp_async16(my_nodes + 32 * k, N + id[k]);
+    }
+    return ok;
+  };
+  unsigned int e = blockIdx.x * T + threadIdx.x;  // this thread's element of tile j
+  issue_conn(e);
+  cp_commit();
+  cp_wait_all();
+  int4 c0 = my_conn[0], c1 = my_conn[T];
+  __syncwarp();
+  issue_conn(e + step);
+  bool ok_next = issue_nodes(e, c0, c1);
+  cp_commit();
+  for (unsigned int j = 0; j < my_tiles; ++j, e += step) {
+    cp_wait_all();  // node records of tile j, connectivity of tile j+1
+    const bool act = e < n, ok = ok_next;
+    V3<float> Y[8];
+    float badw = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float4 h = my_nodes[32 * k];
+      Y[k] = {h.x, h.y, h.z};
+      badw += h.w;
+    }
+    c0 = my_conn[0];
+    c1 = my_conn[T];
+    __syncwarp();  // reads done before the copies below overwrite
+    issue_conn(e + 2 * step);
+    ok_next = issue_nodes(e + step, c0, c1);
+    cp_commit();
     int outcome = -1;
     float lo = 0.f, hi = 0.f;
     if (act) {
-      bool ok = true;
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        ok &= static_cast<uint32_t>(id[k]) < static_cast<uint64_t>(p.n_nodes);
-      if (!ok) {
-        outcome = 5;
-      } else {
-        const float4* N = reinterpret_cast<const float4*>(S.node32);
-        V3<float> Y[8];
-        float badw = 0.f;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          float4 h = __ldg(N + id[k]);
-          Y[k] = {h.x, h.y, h.z};
-          badw += h.w;
-        }
-        outcome = fp32_decide<true>(Y, fabsmax3(0.f, Y[0]), badw != 0.f, lo, hi);
-      }
+      outcome = ok ? fp32_decide<true>(Y, fabsmax3(0.f, Y[0]), badw != 0.f, lo, hi) : 5;
     }
     const bool want_e = act && outcome == 3;
-    escalate(p, want_e, i, warp_scratch());
+    escalate(p, want_e, e, wsc);
     if (act && !want_e) {
+      const int64_t g = p.base + static_cast<int64_t>(e);
       if (outcome == 5) {
         p.flags[g] = make_flag(kVUndecided, 0, 0);
         set_status(S.status, kSbIndex);
@@ -273,16 +321,19 @@ __global__ void __launch_bounds__(kBulkThreads) bulk32p_kernel(Batch p) {
       }
     }
   }
+  cp_wait_all();
 }
 
-int bulk32p_blocks(int threads) {
+int bulk32s_blocks(int threads) {
   static int cached_threads = -1, blocks = 0;
   if (threads != cached_threads) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bulk32p_kernel, threads,
-                                                  scratch_bytes(threads));
+    cudaFuncSetAttribute(bulk32s_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(staged_bytes(kBulkThreads)));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, bulk32s_kernel, threads,
+                                                  staged_bytes(threads));
     blocks = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
     cached_threads = threads;
   }
@@ -530,12 +581,12 @@ cudaError_t launch_bulk32(const Batch& p, cudaStream_t st) {
       bulk32x2_kernel<false><<<blocks, bt, scratch_bytes(bt), st>>>(p);
     return cudaGetLastError();
   }
-  const int bt = p.bulk_threads ? p.bulk_threads : kBulkThreads;
+  const int bt = p.bulk_threads ? p.bulk_threads : kBulk32Default;
   if (p.indexed && p.prefetch32) {
     int64_t need = (p.n + bt - 1) / bt;
-    int64_t blocks = bulk32p_blocks(bt);
-    bulk32p_kernel<<<static_cast<unsigned int>(need < blocks ? need : blocks), bt,
-                     scratch_bytes(bt), st>>>(p);
+    int64_t blocks = bulk32s_blocks(bt);
+    bulk32s_kernel<<<static_cast<unsigned int>(need < blocks ? need : blocks), bt,
+                     staged_bytes(bt), st>>>(p);
     return cudaGetLastError();
   }
   unsigned int blocks = static_cast<unsigned int>((p.n + bt - 1) / bt);

@@ -32,6 +32,7 @@
 // combinations; one level adds at most 6 roundings of size u M0).
 #include "element64.cuh"
 #include "exact.cuh"
+#include "exact_warp.cuh"
 #include "warp_items.cuh"
 
 namespace hexval {
@@ -263,6 +264,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
     return;
   }
   __shared__ double wsm[kTailThreads / 32][kWarpScratch];
+  static_assert(exact_tier::kFastWords <= 2 * kWarpScratch, "warp scratch too small");
   double* mysm = wsm[threadIdx.x >> 5];
   const unsigned int warp_items = kWarpItemsMax * gridDim.x * (blockDim.x >> 5);
   unsigned int epoch = 0;
@@ -295,14 +297,25 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
     if (exact) grid_barrier(&C->arrive, epoch, S.status);
   }
   unsigned int nx = 0;
-  if (exact) {  // phase X: lane 0 of the first kWorkers warps, one element at a time each
+  if (exact) {
+    // phase X: the first kWorkers warps, one element at a time each; depth-0
+    // decisions by the whole warp, anything deeper by lane 0 (full tier)
     nx = min(ldcg(&C->exact_count), static_cast<unsigned int>(S.exact_cap));
     const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
-    if ((threadIdx.x & 31u) == 0u)
-      for (unsigned int w = blockIdx.x + gridDim.x * (threadIdx.x >> 5); w < exact_tier::kWorkers;
-           w += nwarps)
-        for (unsigned int i = w; i < nx; i += exact_tier::kWorkers)
-          exact_tier::exact_element(p, ldcg(S.exact_list + i), w);
+    uint32_t* esm = reinterpret_cast<uint32_t*>(mysm);
+    for (unsigned int w = blockIdx.x + gridDim.x * (threadIdx.x >> 5); w < exact_tier::kWorkers;
+         w += nwarps)
+      for (unsigned int i = w; i < nx; i += exact_tier::kWorkers) {
+        const uint32_t e = ldcg(S.exact_list + i);
+        const int flag = exact_tier::exact_depth0_warp(p, e, esm);
+        if ((threadIdx.x & 31u) == 0u) {
+          if (flag >= 0)
+            p.flags[p.base + e] = static_cast<uint8_t>(flag | 0x80);
+          else
+            exact_tier::exact_element(p, e, w);
+        }
+        __syncwarp();
+      }
   }
   // the last block ends the batch
   __syncthreads();

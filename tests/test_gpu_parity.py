@@ -312,6 +312,37 @@ def test_fp32_variants_agree(kind):
         v.close()
 
 
+@pytest.mark.parametrize("threads", [64, 128, 256])
+def test_staged_indexed_pass_many_tiles(threads):
+    """The indexed FP32 pass staged through shared memory (persistent grid,
+    several tiles per block, a ragged last tile): flags equal to the oracle's,
+    bad connectivity rows flagged, escalations beyond the in-pass share (more
+    than 4096) left to the tail kernel."""
+    nodes, conn = synth.structured_grid(100, 97, 61, sigma=0.3, seed=81)
+    conn = conn.copy()
+    bad_rows = [5, 123_457, len(conn) - 1]
+    good = conn[[6, 123_458, len(conn) - 2]].copy()
+    conn[bad_rows[0], 2] = -7
+    conn[bad_rows[1], 5] = nodes.shape[0]
+    conn[bad_rows[2], 7] = 1 << 30
+    v = hv.Validator(precision="fp32", max_depth=8, options=hv.OPT_PREFETCH,
+                     bulk_threads=threads, **CAPS)
+    v.stats(reset=True)
+    f, lo, hi = [t.cpu().numpy() for t in v.check_indexed(torch.from_numpy(nodes).cuda(),
+                                                          torch.from_numpy(conn).cuda())]
+    assert v.status() == -4  # HEXVAL_E_INDEX
+    st = v.stats()
+    assert st["escalated_fp64"] > 4096
+    assert all(f[r] & 7 == 3 and np.isnan(lo[r]) for r in bad_rows)
+    fixed = conn.copy()
+    fixed[bad_rows] = good
+    want = oracle.check_indexed(nodes, fixed, max_depth=8)
+    ok = np.ones(len(conn), bool)
+    ok[bad_rows] = False
+    _compare("fp32", (f[ok], lo[ok], hi[ok]), tuple(w[ok] for w in want))
+    v.close()
+
+
 def test_autotuner_picks_a_candidate_and_stays_exact(tmp_path):
     from paper_1706_01613_gb300 import tune
     nodes, conn = synth.structured_grid(40, 40, 40, sigma=0.15, seed=80)
