@@ -49,27 +49,33 @@ def workload(cfg, rank):
         nodes, conn = synth.structured_grid(128, seed=20170002 + 1000 * rank)
         return dict(kind="indexed", nodes=nodes, conn=conn, n=conn.shape[0], depth=8,
                     name="structured mesh 128^3 hexes (129^3 FP64 nodes, sigma 0.15, int32 conn)",
-                    bytes_per_hex=32 + 17, node_bytes=24 * nodes.shape[0])
+                    bytes_per_hex=32 + 17, n_nodes=nodes.shape[0])
     if cfg == 1:
         X = synth.perturbed_cubes(10_000, seed=20170001 + 1000 * rank)
         return dict(kind="soa", X=X, n=X.shape[2], depth=8,
                     name="10,000 perturbed unit cubes (U[-0.3,0.3], SoA FP64)",
-                    bytes_per_hex=192 + 17, node_bytes=0)
+                    bytes_per_hex=192 + 17, n_nodes=0)
     if cfg == 3:
         X, _, _ = synth.affine_mixture(16_777_216, seed=20170003 + 1000 * rank)
         return dict(kind="soa", X=X, n=X.shape[2], depth=8,
                     name="16,777,216 affine / near-degenerate / inverted hexes (SoA FP64)",
-                    bytes_per_hex=192 + 17, node_bytes=0)
+                    bytes_per_hex=192 + 17, n_nodes=0)
     if cfg == 4:
         X = synth.twisted_layers(4_194_304, seed=20170004 + 1000 * rank)
         return dict(kind="soa", X=X, n=X.shape[2], depth=10,
                     name="4,194,304 twisted boundary-layer hexes (SoA FP64, depth cap 10)",
-                    bytes_per_hex=192 + 17, node_bytes=0)
+                    bytes_per_hex=192 + 17, n_nodes=0)
     raise ValueError(cfg)
 
 
-def algorithmic_bytes(w):
-    return w["bytes_per_hex"] * w["n"] + w["node_bytes"]
+def algorithmic_bytes(w, kernel):
+    """Bytes a launch of `kernel` must move: bulk32 reads the connectivity
+    (32 B/hex) or the 24 FP64 coordinates (192 B/hex), writes 17 B/hex
+    (flag, bmin, bmax), and in the indexed form reads each 16-byte FP32 node
+    record once; nodes32 reads 24 B and writes 16 B per node."""
+    if kernel == "nodes32":
+        return 40 * w["n_nodes"]
+    return w["bytes_per_hex"] * w["n"] + 16 * w["n_nodes"]
 
 
 # ------------------------------------------------------------ clock probe ---
@@ -296,6 +302,49 @@ def reference_arm(args, w):
                     "d2h_bytes_per_step": 0}}
 
 
+def quad_run(steps, warmup, flush):
+    """Linear quadrangles (Sec. 2.1): a 4096^2 structured 2D mesh (indexed),
+    FP32-filtered and FP64 forms, device-resident inputs, L2 flushed between
+    calls; CUDA events per call on the launch stream."""
+    import torch
+    from paper_1706_01613_gb300 import hexval as hv
+    from paper_1706_01613_gb300 import synth
+    nodes, conn = synth.structured_grid_2d(4096)
+    N, C = torch.from_numpy(nodes).cuda(), torch.from_numpy(conn).cuda()
+    n = conn.shape[0]
+    out = {}
+    for prec in ("fp32", "fp64"):
+        v = hv.Validator(precision=prec, queue_capacity=1 << 10, max_batch=1 << 10,
+                         max_nodes=1 << 10, exact_capacity=1 << 10)
+        res = (torch.empty(n, dtype=torch.uint8, device="cuda"),
+               torch.empty(n, dtype=torch.float64, device="cuda"),
+               torch.empty(n, dtype=torch.float64, device="cuda"))
+        for _ in range(warmup):
+            flush.zero_()
+            v.check_quads_indexed(N, C, out=res)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record()
+            v.check_quads_indexed(N, C, out=res)
+            b.record()
+        torch.cuda.synchronize()
+        v.raise_on_status()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        out[prec] = (n / (ms / 1e3), ms)
+        v.close()
+    abytes = (16 + 17) * n + 16 * nodes.shape[0]
+    hbm, kind = peaks()
+    achieved = abytes / (out["fp32"][1] / 1e3) / 1e9
+    return {"workload": "4096^2 structured 2D mesh (4097^2 FP64 nodes, sigma 0.15, int32 conn)",
+            "n_quad": n, "value": out["fp32"][0], "unit": "quad/s", "ms_per_call": out["fp32"][1],
+            "fp64": {"value": out["fp64"][0], "unit": "quad/s", "ms_per_call": out["fp64"][1]},
+            "roofline": {"bound": "hbm", "kernel": "quad32", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "peak_kind": kind + " (hbm_gbs)",
+                         "algorithmic_bytes_per_launch": abytes, "traffic": None}}
+
+
 def serving_run(precision, rate, n_requests, pool, slots=4, budget=40 << 30, seed=20175000):
     """One continuous-batching run: Poisson arrivals at `rate`/s, sizes
     log-uniform in [100, pool size]; returns the latency summary."""
@@ -346,6 +395,11 @@ def main():
     ap.add_argument("--serve-max-n", type=int, default=1_000_000)
     ap.add_argument("--retune", action="store_true",
                     help="time every launch configuration again instead of using the cache")
+    ap.add_argument("--bulk-threads", type=int, default=None,
+                    help="fixed FP32 launch configuration instead of the autotuner's")
+    ap.add_argument("--options", type=int, default=0, help="options with --bulk-threads")
+    ap.add_argument("--no-quads", dest="quads", action="store_false",
+                    help="skip the quadrangle measurement")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -393,8 +447,11 @@ def main():
     # launch configuration of the FP32 form from the autotuner (timed here on
     # this workload, cached per device and shape)
     from paper_1706_01613_gb300 import tune
-    tuned = tune.best_config("fp32", w["kind"], w["n"], dev_in, retune=args.retune,
-                             max_depth=w["depth"])
+    if args.bulk_threads is not None:  # fixed launch configuration (profiling runs)
+        tuned = {"options": args.options, "bulk_threads": args.bulk_threads}
+    else:
+        tuned = tune.best_config("fp32", w["kind"], w["n"], dev_in, retune=args.retune,
+                                 max_depth=w["depth"])
     v32 = hv.Validator(precision="fp32", max_depth=w["depth"], **tuned)
     v64 = hv.Validator(precision="fp64", max_depth=w["depth"])
 
@@ -436,9 +493,7 @@ def main():
     dom_ms = phases[dom][0] / phases[dom][1]
     hbm, peak_kind = peaks()
     if dom in ("bulk32", "nodes32"):
-        abytes = algorithmic_bytes(w)
-        if dom == "nodes32":
-            abytes = w["node_bytes"] + 32 * (w["node_bytes"] // 24)
+        abytes = algorithmic_bytes(w, dom)
         achieved = abytes / (dom_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
                 "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind + " (hbm_gbs)",
@@ -469,6 +524,8 @@ def main():
     pool = serve.Pool(args.serve_max_n)
     latency = serving_run("fp32", 300, 150, pool)
 
+    quads = quad_run(max(5, args.steps // 20), 3, flush) if args.quads else None
+
     launches_per_step = sum(v[1] for v in phases.values()) / args.steps
     rec = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -492,6 +549,7 @@ def main():
         "stats_fp32": st32,
         "cpu_baseline": cpu,
         "latency": latency,
+        "quads": quads,
         "clocks": clocks.summary(*window),
     }
     print(json.dumps(rec))

@@ -133,6 +133,54 @@ int hexval_check_indexed(hexval_handle h, int64_t n_nodes, const double* nodes, 
                          const int32_t* conn, uint8_t* flags, double* bmin, double* bmax,
                          void* stream);
 
+/* Validity of linear quadrangles (Sec. 2.1, Eq. e:determinant2D): the
+ * Jacobian determinant of the bilinear map is bilinear, so the element is
+ * valid iff its values at the four corners are all positive (strictly).
+ * Nodes 1..4 at reference (0,0), (1,0), (1,1), (0,1).
+ *
+ * corners: device, FP64, planes [4][2][n_quad] (plane 2k + d = coordinate d
+ * of node k).  flags: device, n_quad bytes, verdict VALID / INVALID /
+ * NONFINITE (or UNDECIDED with status HEXVAL_E_RANGE when an exact test is
+ * needed on coordinates spanning more than 120 bits), depth 0, bit 7 set
+ * when the exact test decided.  jmin / jmax (device, may be NULL): min / max
+ * of the four corner values (FP32-accurate for elements decided by the FP32
+ * filter of a HEXVAL_FP32_FILTERED handle, else FP64).  The handle's
+ * precision selects the form; the flags are the exact-arithmetic ones in
+ * both.  Stream-ordered, no allocation; errors as hexval_check_soa. */
+int hexval_check_quads(hexval_handle h, int64_t n_quad, const double* corners, uint8_t* flags,
+                       double* jmin, double* jmax, void* stream);
+
+/* The same for an indexed 2D mesh: nodes [n_nodes][2] FP64 and conn
+ * [n_quad][4] int32 (0-based, node order as above), both device and 16-byte
+ * aligned (else HEXVAL_E_ARG).  An out-of-range entry gives that element
+ * UNDECIDED with NaN jmin / jmax and the sticky status HEXVAL_E_INDEX. */
+int hexval_check_quads_indexed(hexval_handle h, int64_t n_nodes, const double* nodes,
+                               int64_t n_quad, const int32_t* conn, uint8_t* flags, double* jmin,
+                               double* jmax, void* stream);
+
+/* Corner scaled Jacobian, the quality measure quoted in Sec. 7 (Fig.
+ * f:invalidHighCornerQual): per element the minimum over its 8 corners of
+ * the determinant of the three edge vectors leaving the corner, each
+ * divided by its length (0 at a corner with a zero-length edge; in [-1, 1]).
+ * It is not a validity test: the figure shows an invalid element whose
+ * value is 0.64.
+ *
+ * corners: device FP64 planes [8][3][n_hex] as for hexval_check_soa.
+ * sj_min: device, n_hex floats; NaN for non-finite input.  Computed in FP32
+ * from the coordinates relative to node 1 (formed in FP64 and scaled by a
+ * power of two), so it does not depend on where the element sits; error
+ * about 1e-6 for elements of moderate aspect ratio.  Independent of the
+ * handle's precision.  Stream-ordered, no allocation. */
+int hexval_corner_quality(hexval_handle h, int64_t n_hex, const double* corners, float* sj_min,
+                          void* stream);
+
+/* The same on an indexed mesh (nodes [n_nodes][3] FP64, conn [n_hex][8]
+ * int32, 16-byte aligned); an out-of-range entry gives NaN and the sticky
+ * status HEXVAL_E_INDEX. */
+int hexval_corner_quality_indexed(hexval_handle h, int64_t n_nodes, const double* nodes,
+                                  int64_t n_hex, const int32_t* conn, float* sj_min,
+                                  void* stream);
+
 /* Synchronises the stream, returns the sticky device status (HEXVAL_OK or
  * the most severe device-detected code) and clears it. */
 int hexval_status(hexval_handle h, void* stream);

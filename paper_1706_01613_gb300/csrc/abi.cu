@@ -249,6 +249,89 @@ int hexval_check_indexed(hexval_handle h, int64_t n_nodes, const double* nodes, 
   return run_batches(h, p, n_hex, st);
 }
 
+int hexval_check_quads(hexval_handle h, int64_t n_quad, const double* corners, uint8_t* flags,
+                       double* jmin, double* jmax, void* stream) {
+  if (!h || n_quad < 0) return HEXVAL_E_ARG;
+  if (n_quad == 0) return HEXVAL_OK;
+  if (!corners || !flags) return HEXVAL_E_ARG;
+  if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;
+  hexval::QuadBatch q{};
+  q.n = n_quad;
+  q.soa = corners;
+  q.stride = n_quad;
+  q.indexed = 0;
+  q.flags = flags;
+  q.jmin = jmin;
+  q.jmax = jmax;
+  q.status = h->s.status;
+  return hexval::launch_quads(q, h->cfg.precision == HEXVAL_FP32_FILTERED,
+                              static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? HEXVAL_OK
+             : HEXVAL_E_CUDA;
+}
+
+int hexval_check_quads_indexed(hexval_handle h, int64_t n_nodes, const double* nodes,
+                               int64_t n_quad, const int32_t* conn, uint8_t* flags, double* jmin,
+                               double* jmax, void* stream) {
+  if (!h || n_quad < 0 || n_nodes < 0 || n_nodes >= (1ll << 31)) return HEXVAL_E_ARG;
+  if (n_quad == 0) return HEXVAL_OK;
+  if (!nodes || !conn || !flags || n_nodes == 0) return HEXVAL_E_ARG;
+  if (reinterpret_cast<uintptr_t>(conn) % 16 != 0 || reinterpret_cast<uintptr_t>(nodes) % 16 != 0)
+    return HEXVAL_E_ARG;  // int4 rows, double2 nodes
+  if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;
+  hexval::QuadBatch q{};
+  q.n = n_quad;
+  q.nodes = nodes;
+  q.n_nodes = n_nodes;
+  q.conn = conn;
+  q.indexed = 1;
+  q.flags = flags;
+  q.jmin = jmin;
+  q.jmax = jmax;
+  q.status = h->s.status;
+  return hexval::launch_quads(q, h->cfg.precision == HEXVAL_FP32_FILTERED,
+                              static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? HEXVAL_OK
+             : HEXVAL_E_CUDA;
+}
+
+int hexval_corner_quality(hexval_handle h, int64_t n_hex, const double* corners, float* sj_min,
+                          void* stream) {
+  if (!h || n_hex < 0 || n_hex >= (1ll << 31)) return HEXVAL_E_ARG;
+  if (n_hex == 0) return HEXVAL_OK;
+  if (!corners || !sj_min) return HEXVAL_E_ARG;
+  if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;
+  Batch p{};
+  p.n = n_hex;
+  p.soa = corners;
+  p.stride = n_hex;
+  p.s = h->s;
+  return hexval::launch_quality(p, sj_min, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? HEXVAL_OK
+             : HEXVAL_E_CUDA;
+}
+
+int hexval_corner_quality_indexed(hexval_handle h, int64_t n_nodes, const double* nodes,
+                                  int64_t n_hex, const int32_t* conn, float* sj_min,
+                                  void* stream) {
+  if (!h || n_hex < 0 || n_hex >= (1ll << 31) || n_nodes < 0 || n_nodes >= (1ll << 31))
+    return HEXVAL_E_ARG;
+  if (n_hex == 0) return HEXVAL_OK;
+  if (!nodes || !conn || !sj_min || n_nodes == 0) return HEXVAL_E_ARG;
+  if (reinterpret_cast<uintptr_t>(conn) % 16 != 0) return HEXVAL_E_ARG;
+  if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;
+  Batch p{};
+  p.n = n_hex;
+  p.nodes = nodes;
+  p.n_nodes = n_nodes;
+  p.conn = conn;
+  p.indexed = 1;
+  p.s = h->s;
+  return hexval::launch_quality(p, sj_min, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? HEXVAL_OK
+             : HEXVAL_E_CUDA;
+}
+
 int hexval_status(hexval_handle h, void* stream) {
   if (!h) return HEXVAL_E_ARG;
   if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;

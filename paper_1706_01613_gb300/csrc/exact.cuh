@@ -332,7 +332,7 @@ struct Exact {
 
 // Decides element e of the batch exactly and writes its flag (exact bit
 // set).  `worker` < kWorkers selects the working storage.
-__device__ __noinline__ void exact_element(const Batch& p, uint32_t e, uint32_t worker) {
+static __device__ __noinline__ void exact_element(const Batch& p, uint32_t e, uint32_t worker) {
   const Scratch& S = p.s;
   Ws ws{S.exact_work, worker};
   int64_t g = p.base + e;

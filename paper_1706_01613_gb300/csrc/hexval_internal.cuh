@@ -518,12 +518,29 @@ __device__ __forceinline__ void edges_from_nodes(const V3<T> X[8], V3<T> a[4], V
     for (int x = 0; x < 2; ++x) g[x + 2 * y] = vsub(X[node_at(x, y, 1)], X[node_at(x, y, 0)]);
 }
 
+// A batch of linear quadrangles (Sec. 2.1).
+struct QuadBatch {
+  int64_t n;
+  const double* soa;  // [4][2][stride] planes, or
+  int64_t stride;
+  const double* nodes;  // [n_nodes][2] (16-byte aligned) with
+  int64_t n_nodes;
+  const int32_t* conn;  // [n][4] (16-byte aligned)
+  int indexed;
+  uint8_t* flags;
+  double* jmin;
+  double* jmax;
+  uint32_t* status;
+};
+
 // ------------------------------------------------------------- launches ----
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_bulk64(const Batch& p, cudaStream_t st);
 cudaError_t launch_bulk32(const Batch& p, cudaStream_t st);
 cudaError_t launch_nodes32(const Batch& p, cudaStream_t st);
 cudaError_t launch_tail(const Batch& p, bool from_list, cudaStream_t st);
+cudaError_t launch_quads(const QuadBatch& p, bool fp32, cudaStream_t st);
+cudaError_t launch_quality(const Batch& p, float* sj, cudaStream_t st);
 uint64_t exact_work_words();
 
 }  // namespace hexval

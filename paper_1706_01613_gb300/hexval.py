@@ -27,7 +27,9 @@ VALID, INVALID, UNDECIDED, NONFINITE = 1, 2, 3, 4
 # every function declared in include/hexval.h (the CPU test checks the list)
 EXPORTS = ("hexval_config_default", "hexval_create", "hexval_destroy", "hexval_check_soa",
            "hexval_check_indexed", "hexval_status", "hexval_get_stats", "hexval_profile_enable",
-           "hexval_profile_read", "hexval_check_soa_noalloc", "hexval_strerror")
+           "hexval_profile_read", "hexval_check_soa_noalloc", "hexval_check_quads",
+           "hexval_check_quads_indexed", "hexval_corner_quality",
+           "hexval_corner_quality_indexed", "hexval_strerror")
 PHASES = ("nodes32", "bulk32", "bulk64", "tail", "exact", "-", "-", "-")
 
 
@@ -86,6 +88,10 @@ def load(build_if_missing=False):
     lib.hexval_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.hexval_profile_read.argtypes = [vp, ctypes.POINTER(Profile), ctypes.c_int]
     lib.hexval_check_soa_noalloc.argtypes = [i64, vp, vp, vp, vp, ctypes.c_int32, vp, vp]
+    lib.hexval_check_quads.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    lib.hexval_check_quads_indexed.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, vp]
+    lib.hexval_corner_quality.argtypes = [vp, i64, vp, vp, vp]
+    lib.hexval_corner_quality_indexed.argtypes = [vp, i64, vp, i64, vp, vp, vp]
     lib.hexval_strerror.argtypes = [ctypes.c_int]
     lib.hexval_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -203,6 +209,68 @@ class Validator:
                                             self._ptr(bmax), _stream_ptr(stream))
         _check(rc, "hexval_check_indexed")
         return flags, bmin, bmax
+
+    def check_quads(self, corners, out=None, stream=None):
+        """Linear quadrangles: corners contiguous float64 CUDA (4, 2, n).
+        Returns (flags uint8, jmin float64, jmax float64)."""
+        import torch
+        if corners.dtype != torch.float64 or not corners.is_cuda or not corners.is_contiguous():
+            raise ValueError("corners must be a contiguous float64 CUDA tensor (4, 2, n)")
+        if corners.dim() != 3 or tuple(corners.shape[:2]) != (4, 2):
+            raise ValueError("corners must have shape (4, 2, n)")
+        n = corners.shape[2]
+        flags, jmin, jmax = self._outputs(n, out)
+        rc = self._lib.hexval_check_quads(self._h, n, self._ptr(corners), self._ptr(flags),
+                                          self._ptr(jmin), self._ptr(jmax), _stream_ptr(stream))
+        _check(rc, "hexval_check_quads")
+        return flags, jmin, jmax
+
+    def check_quads_indexed(self, nodes, conn, out=None, stream=None):
+        """nodes: float64 CUDA (n_nodes, 2); conn: int32 CUDA (n_quad, 4)."""
+        import torch
+        if nodes.dtype != torch.float64 or not nodes.is_cuda or not nodes.is_contiguous():
+            raise ValueError("nodes must be a contiguous float64 CUDA tensor (n_nodes, 2)")
+        if conn.dtype != torch.int32 or not conn.is_cuda or not conn.is_contiguous():
+            raise ValueError("conn must be a contiguous int32 CUDA tensor (n_quad, 4)")
+        if nodes.dim() != 2 or nodes.shape[1] != 2 or conn.dim() != 2 or conn.shape[1] != 4:
+            raise ValueError("bad shapes")
+        n = conn.shape[0]
+        flags, jmin, jmax = self._outputs(n, out)
+        rc = self._lib.hexval_check_quads_indexed(self._h, nodes.shape[0], self._ptr(nodes), n,
+                                                  self._ptr(conn), self._ptr(flags),
+                                                  self._ptr(jmin), self._ptr(jmax),
+                                                  _stream_ptr(stream))
+        _check(rc, "hexval_check_quads_indexed")
+        return flags, jmin, jmax
+
+    def corner_quality(self, corners, out=None, stream=None):
+        """Minimum corner scaled Jacobian of each element; corners as for
+        check_soa.  Returns a float32 CUDA tensor (n,)."""
+        import torch
+        if corners.dtype != torch.float64 or not corners.is_cuda or not corners.is_contiguous():
+            raise ValueError("corners must be a contiguous float64 CUDA tensor (8, 3, n)")
+        if corners.dim() != 3 or tuple(corners.shape[:2]) != (8, 3):
+            raise ValueError("corners must have shape (8, 3, n)")
+        n = corners.shape[2]
+        sj = out if out is not None else torch.empty(n, dtype=torch.float32, device=corners.device)
+        rc = self._lib.hexval_corner_quality(self._h, n, self._ptr(corners), self._ptr(sj),
+                                             _stream_ptr(stream))
+        _check(rc, "hexval_corner_quality")
+        return sj
+
+    def corner_quality_indexed(self, nodes, conn, out=None, stream=None):
+        """Minimum corner scaled Jacobian on an indexed mesh (float32 (n,))."""
+        import torch
+        if nodes.dtype != torch.float64 or conn.dtype != torch.int32 or not nodes.is_cuda \
+                or not conn.is_cuda or not nodes.is_contiguous() or not conn.is_contiguous():
+            raise ValueError("nodes: contiguous float64 CUDA (n_nodes, 3); conn: int32 (n, 8)")
+        n = conn.shape[0]
+        sj = out if out is not None else torch.empty(n, dtype=torch.float32, device=nodes.device)
+        rc = self._lib.hexval_corner_quality_indexed(self._h, nodes.shape[0], self._ptr(nodes), n,
+                                                     self._ptr(conn), self._ptr(sj),
+                                                     _stream_ptr(stream))
+        _check(rc, "hexval_corner_quality_indexed")
+        return sj
 
     def check_host(self, kind, *arrays, stream=None):
         """End-to-end call on host data: copies the inputs (pinned host

@@ -172,3 +172,40 @@ def request_inputs(req):
         return ("indexed", nodes, conn)
     X, _, _ = affine_mixture(n, seed=seed)
     return ("soa", X)
+
+
+# ------------------------------------------------------------ quadrangles --
+# Layouts: SoA float64 (4, 2, n) (plane [k][d] = coordinate d of node k,
+# nodes 1..4 at reference (0,0), (1,0), (1,1), (0,1)); indexed: nodes
+# float64 (n_nodes, 2), conn int32 (n, 4).
+REF_SQUARE = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], dtype=np.float64)
+
+
+def perturbed_squares(n, noise=0.3, seed=None):
+    """Unit-square corners with every coordinate perturbed by i.i.d.
+    U[-noise, noise] (seed 20170006 by default)."""
+    rng = rng_for(6, seed)
+    X = np.broadcast_to(REF_SQUARE[:, :, None], (4, 2, n)).copy()
+    X += rng.uniform(-noise, noise, size=(4, 2, n))
+    return X
+
+
+def structured_grid_2d(nx=4096, ny=None, sigma=0.15, seed=None):
+    """(nx+1)(ny+1) nodes of spacing 1, interior nodes displaced by i.i.d.
+    N(0, sigma^2) per axis (seed 20170007 by default).  Node id i + (nx+1) j;
+    quad (i, j) has index i + nx j.  Returns (nodes (n_nodes, 2) f64,
+    conn (n, 4) i32)."""
+    ny = nx if ny is None else ny
+    rng = rng_for(7, seed)
+    px, py = nx + 1, ny + 1
+    j, i = np.meshgrid(np.arange(py), np.arange(px), indexing="ij")
+    nodes = np.stack([i, j], axis=-1).reshape(-1, 2).astype(np.float64)
+    disp = rng.normal(0.0, sigma, size=nodes.shape)
+    ii, jj = i.reshape(-1), j.reshape(-1)
+    interior = (ii > 0) & (ii < nx) & (jj > 0) & (jj < ny)
+    nodes[interior] += disp[interior]
+    qj, qi = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    qi, qj = qi.reshape(-1), qj.reshape(-1)
+    conn = np.stack([qi + px * qj, qi + 1 + px * qj, qi + 1 + px * (qj + 1), qi + px * (qj + 1)],
+                    axis=1).astype(np.int32)
+    return nodes, conn
