@@ -345,6 +345,46 @@ def quad_run(steps, warmup, flush):
                          "algorithmic_bytes_per_launch": abytes, "traffic": None}}
 
 
+def filter_run(steps, warmup, flush):
+    """Candidate filtering: 40 candidate hexahedra per node over a 65^3 node
+    array (cells of a perturbed grid relabelled by random cube symmetries),
+    FP32-filtered check + compaction of the valid ids, per call with CUDA
+    events, L2 flushed between calls."""
+    import torch
+    from paper_1706_01613_gb300 import hexval as hv
+    from paper_1706_01613_gb300 import synth
+    nodes, conn, _, _ = synth.hex_candidates()
+    N, C = torch.from_numpy(nodes).cuda(), torch.from_numpy(conn).cuda()
+    n = conn.shape[0]
+    v = hv.Validator(precision="fp32", max_depth=8)
+    flags = torch.empty(n, dtype=torch.uint8, device="cuda")
+    out = (torch.empty(n, dtype=torch.int32, device="cuda"),
+           torch.empty(1, dtype=torch.int32, device="cuda"))
+
+    def call():
+        v.check_indexed(N, C, out=(flags, None, None))
+        v.compact(flags, (hv.VALID,), out=out)
+
+    for _ in range(warmup):
+        flush.zero_()
+        call()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        call()
+        b.record()
+    torch.cuda.synchronize()
+    v.raise_on_status()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    kept = int(out[1].item())
+    v.close()
+    return {"workload": "%d candidate hexes over %d nodes (40 per node, cube-symmetry relabelled "
+                        "cells of a perturbed 64^3 grid)" % (n, nodes.shape[0]),
+            "value": n / (ms / 1e3), "unit": "candidate/s", "ms_per_call": ms, "kept": kept}
+
+
 def serving_run(precision, rate, n_requests, pool, slots=4, budget=40 << 30, seed=20175000):
     """One continuous-batching run: Poisson arrivals at `rate`/s, sizes
     log-uniform in [100, pool size]; returns the latency summary."""
@@ -399,7 +439,7 @@ def main():
                     help="fixed FP32 launch configuration instead of the autotuner's")
     ap.add_argument("--options", type=int, default=0, help="options with --bulk-threads")
     ap.add_argument("--no-quads", dest="quads", action="store_false",
-                    help="skip the quadrangle measurement")
+                    help="skip the quadrangle and candidate-filtering measurements")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -525,6 +565,7 @@ def main():
     latency = serving_run("fp32", 300, 150, pool)
 
     quads = quad_run(max(5, args.steps // 20), 3, flush) if args.quads else None
+    filt = filter_run(max(5, args.steps // 50), 3, flush) if args.quads else None
 
     launches_per_step = sum(v[1] for v in phases.values()) / args.steps
     rec = {
@@ -550,6 +591,7 @@ def main():
         "cpu_baseline": cpu,
         "latency": latency,
         "quads": quads,
+        "filter": filt,
         "clocks": clocks.summary(*window),
     }
     print(json.dumps(rec))

@@ -181,6 +181,17 @@ int hexval_corner_quality_indexed(hexval_handle h, int64_t n_nodes, const double
                                   int64_t n_hex, const int32_t* conn, float* sj_min,
                                   void* stream);
 
+/* Stream compaction by verdict, for candidate filtering (the paper's
+ * motivating use, Sec. 1: indirect hex-dominant meshing builds candidate
+ * hexahedra, many more than there are vertices, and keeps the valid ones).
+ * Writes to ids (device, capacity n) the indices i, in ascending order, whose
+ * verdict flags[i] & 7 has its bit set in verdict_mask (bit 1 = VALID, bit 2
+ * = INVALID, ...), and their number to *count (device).  flags: device, n
+ * bytes (the output of a check).  n < 2^31.  Stream-ordered, no allocation
+ * (the tile sums live in the handle); errors as hexval_check_soa. */
+int hexval_compact(hexval_handle h, int64_t n, const uint8_t* flags, uint32_t verdict_mask,
+                   int32_t* ids, int32_t* count, void* stream);
+
 /* Synchronises the stream, returns the sticky device status (HEXVAL_OK or
  * the most severe device-detected code) and clears it. */
 int hexval_status(hexval_handle h, void* stream);

@@ -165,7 +165,9 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
             alloc(h, &s.slot_m0, s.qcap) && alloc(h, &s.esc, cfg->max_batch) &&
             alloc(h, &s.exact_list, s.exact_cap) && alloc(h, &s.exact_work, s.exact_work_words) &&
             alloc(h, &s.node32, 4 * s.max_nodes) && alloc(h, &s.cnt, 1) &&
-            alloc(h, &s.stats, 1) && alloc(h, &s.status, 1);
+            alloc(h, &s.stats, 1) && alloc(h, &s.status, 1) &&
+            alloc(h, &s.tiles, static_cast<uint64_t>(hexval::compact_tiles(1ll << 31)));
+  s.tiles_cap = static_cast<uint64_t>(hexval::compact_tiles(1ll << 31));
   if (!ok) {
     free_all(h);
     delete h;
@@ -328,6 +330,17 @@ int hexval_corner_quality_indexed(hexval_handle h, int64_t n_nodes, const double
   p.indexed = 1;
   p.s = h->s;
   return hexval::launch_quality(p, sj_min, static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? HEXVAL_OK
+             : HEXVAL_E_CUDA;
+}
+
+int hexval_compact(hexval_handle h, int64_t n, const uint8_t* flags, uint32_t verdict_mask,
+                   int32_t* ids, int32_t* count, void* stream) {
+  if (!h || n < 0 || n >= (1ll << 31) || !count || (verdict_mask & ~0xffu)) return HEXVAL_E_ARG;
+  if (n > 0 && (!flags || !ids)) return HEXVAL_E_ARG;
+  if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;
+  return hexval::launch_compact(flags, n, verdict_mask, h->s.tiles, ids, count,
+                                static_cast<cudaStream_t>(stream)) == cudaSuccess
              ? HEXVAL_OK
              : HEXVAL_E_CUDA;
 }

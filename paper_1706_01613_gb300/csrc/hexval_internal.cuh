@@ -92,6 +92,9 @@ struct Scratch {
   Counters* cnt;
   Stats* stats;
   uint32_t* status;
+  // prefix sums of the compaction tiles (compact.cu)
+  uint64_t* tiles;
+  uint64_t tiles_cap;
 };
 
 // One batch of elements, as seen by every kernel.
@@ -541,6 +544,9 @@ cudaError_t launch_nodes32(const Batch& p, cudaStream_t st);
 cudaError_t launch_tail(const Batch& p, bool from_list, cudaStream_t st);
 cudaError_t launch_quads(const QuadBatch& p, bool fp32, cudaStream_t st);
 cudaError_t launch_quality(const Batch& p, float* sj, cudaStream_t st);
+int64_t compact_tiles(int64_t n);
+cudaError_t launch_compact(const uint8_t* flags, int64_t n, uint32_t mask, uint64_t* tiles,
+                           int32_t* ids, int32_t* count, cudaStream_t st);
 uint64_t exact_work_words();
 
 }  // namespace hexval

@@ -29,7 +29,7 @@ EXPORTS = ("hexval_config_default", "hexval_create", "hexval_destroy", "hexval_c
            "hexval_check_indexed", "hexval_status", "hexval_get_stats", "hexval_profile_enable",
            "hexval_profile_read", "hexval_check_soa_noalloc", "hexval_check_quads",
            "hexval_check_quads_indexed", "hexval_corner_quality",
-           "hexval_corner_quality_indexed", "hexval_strerror")
+           "hexval_corner_quality_indexed", "hexval_compact", "hexval_strerror")
 PHASES = ("nodes32", "bulk32", "bulk64", "tail", "exact", "-", "-", "-")
 
 
@@ -92,6 +92,7 @@ def load(build_if_missing=False):
     lib.hexval_check_quads_indexed.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, vp]
     lib.hexval_corner_quality.argtypes = [vp, i64, vp, vp, vp]
     lib.hexval_corner_quality_indexed.argtypes = [vp, i64, vp, i64, vp, vp, vp]
+    lib.hexval_compact.argtypes = [vp, i64, vp, ctypes.c_uint32, vp, vp, vp]
     lib.hexval_strerror.argtypes = [ctypes.c_int]
     lib.hexval_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -271,6 +272,35 @@ class Validator:
                                                      _stream_ptr(stream))
         _check(rc, "hexval_corner_quality_indexed")
         return sj
+
+    def compact(self, flags, verdicts=(VALID,), out=None, stream=None):
+        """Ids (int32, ascending) of the elements whose verdict is in
+        `verdicts`, enqueued on `stream`.  Returns (ids buffer of len(flags),
+        count as a one-element int32 CUDA tensor); ids[:count] are valid."""
+        import torch
+        if flags.dtype != torch.uint8 or not flags.is_cuda or not flags.is_contiguous():
+            raise ValueError("flags must be a contiguous uint8 CUDA tensor")
+        n = flags.numel()
+        ids, count = out if out is not None else (
+            torch.empty(max(n, 1), dtype=torch.int32, device=flags.device),
+            torch.empty(1, dtype=torch.int32, device=flags.device))
+        mask = 0
+        for v in verdicts:
+            mask |= 1 << int(v)
+        rc = self._lib.hexval_compact(self._h, n, self._ptr(flags), mask, self._ptr(ids),
+                                      self._ptr(count), _stream_ptr(stream))
+        _check(rc, "hexval_compact")
+        return ids, count
+
+    def filter_valid(self, nodes, conn, stream=None):
+        """Candidate filtering: checks every candidate of an indexed set and
+        returns the ids of the valid ones (synchronises to read the count)."""
+        flags, _, _ = self.check_indexed(nodes, conn, out=self._outputs(conn.shape[0], None)[:1]
+                                         + (None, None), stream=stream)
+        ids, count = self.compact(flags, stream=stream)
+        if stream is not None:
+            stream.synchronize()
+        return ids[:int(count.item())]
 
     def check_host(self, kind, *arrays, stream=None):
         """End-to-end call on host data: copies the inputs (pinned host

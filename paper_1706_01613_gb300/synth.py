@@ -209,3 +209,42 @@ def structured_grid_2d(nx=4096, ny=None, sigma=0.15, seed=None):
     conn = np.stack([qi + px * qj, qi + 1 + px * qj, qi + 1 + px * (qj + 1), qi + px * (qj + 1)],
                     axis=1).astype(np.int32)
     return nodes, conn
+
+
+# ------------------------------------------------------ candidate sets ------
+
+def cube_symmetries():
+    """The 48 symmetries of the reference cube as permutations of the corner
+    labels (Appendix A order), with +1 for the 24 rotations and -1 for the 24
+    orientation-reversing ones.  Returns (perm (48, 8) int, sign (48,) int)."""
+    import itertools
+    ref = REF_CORNERS - 0.5
+    perms, signs = [], []
+    for p in itertools.permutations(range(3)):
+        for s in itertools.product((1.0, -1.0), repeat=3):
+            S = np.zeros((3, 3))
+            for i in range(3):
+                S[i, p[i]] = s[i]
+            img = ref @ S.T
+            perm = [int(np.nonzero(np.all(np.isclose(ref, img[k]), axis=1))[0][0]) for k in range(8)]
+            perms.append(perm)
+            signs.append(int(round(np.linalg.det(S))))
+    return np.array(perms), np.array(signs)
+
+
+def hex_candidates(nx=64, per_node=40, sigma=0.15, seed=None):
+    """A candidate set over one node array, the shape of indirect hex-dominant
+    meshing input (many more candidates than vertices): the nodes of an
+    (nx+1)^3 structured grid with N(0, sigma^2) interior noise, and
+    per_node x n_nodes candidate hexahedra, each a random cell of the grid
+    with its corners relabelled by a random cube symmetry (a rotation keeps
+    the cell's validity, a reflection inverts it).  Seed 20170008 by default.
+    Returns (nodes, conn (n_cand, 8) int32, cell (n_cand,), sym (n_cand,))."""
+    nodes, cells = structured_grid(nx, sigma=sigma, seed=(SEED_BASE + 8) if seed is None else seed)
+    rng = rng_for(8, seed)
+    n = per_node * nodes.shape[0]
+    cell = rng.integers(0, cells.shape[0], size=n)
+    sym = rng.integers(0, 48, size=n)
+    perm, _ = cube_symmetries()
+    conn = np.take_along_axis(cells[cell], perm[sym], axis=1).astype(np.int32)
+    return nodes, conn, cell, sym
