@@ -32,7 +32,7 @@ struct Profiler {
 struct hexval_ctx {
   hexval_config cfg;
   Scratch s;
-  void* blocks[24];
+  void* blocks[48];
   int nblocks;
   Profiler prof;
 };
@@ -50,6 +50,7 @@ template <typename T>
 bool alloc(hexval_ctx* h, T** out, uint64_t count) {
   void* p = nullptr;
   if (count == 0) count = 1;
+  if (h->nblocks >= static_cast<int>(sizeof(h->blocks) / sizeof(h->blocks[0]))) return false;
   if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
     cudaGetLastError();
     return false;
@@ -168,6 +169,15 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
             alloc(h, &s.stats, 1) && alloc(h, &s.status, 1) &&
             alloc(h, &s.tiles, static_cast<uint64_t>(hexval::compact_tiles(1ll << 31)));
   s.tiles_cap = static_cast<uint64_t>(hexval::compact_tiles(1ll << 31));
+  if (ok && cfg->precision == HEXVAL_FP32_FILTERED) {
+    s.q32cap = s.qcap;
+    ok = alloc(h, &s.r32, cfg->max_batch) && alloc(h, &s.esc2, cfg->max_batch) &&
+         alloc(h, &s.q32coef[0], 27 * s.q32cap) && alloc(h, &s.q32coef[1], 27 * s.q32cap) &&
+         alloc(h, &s.q32slot[0], s.q32cap) && alloc(h, &s.q32slot[1], s.q32cap) &&
+         alloc(h, &s.s32_elem, cfg->max_batch) && alloc(h, &s.s32_state, cfg->max_batch) &&
+         alloc(h, &s.s32_lev, cfg->max_batch) && alloc(h, &s.s32_e0, cfg->max_batch) &&
+         alloc(h, &s.s32_m0, cfg->max_batch);
+  }
   if (!ok) {
     free_all(h);
     delete h;

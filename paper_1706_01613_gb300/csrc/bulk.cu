@@ -17,6 +17,7 @@
 // and L the largest |component| among them, every sample and coefficient is
 // within 200 eps L^2 + 740 u L^3 of its exact value; the kernel uses
 // 256 eps L^2 + 1024 u L^3 with eps = 2^-23 X + 2^-24 L, X >= |coordinates|.
+#include "element32.cuh"
 #include "warp_items.cuh"
 
 namespace hexval {
@@ -43,6 +44,44 @@ __device__ __forceinline__ void escalate(const Batch& p, bool want, unsigned int
   }
 }
 
+// Outputs of one element of the FP32 pass (all 32 lanes call it; outcomes of
+// fp32_classify, or 5 for a connectivity entry out of range): escalations go
+// to FP64 (escalate); of the elements to refine, the first kR32InBulk of the
+// batch are redone in FP64 here by the whole warp and the others are listed
+// for the FP32 refinement (their flag comes later); the rest get their
+// verdict here.
+__device__ __forceinline__ void finish32(const Batch& p, bool act, int outcome, unsigned int e,
+                                         float lo, float hi, double* sm) {
+  const Scratch& S = p.s;
+  const bool want_e = act && outcome == 3;
+  escalate(p, want_e, e, sm);
+  const bool want_r = act && outcome == 2 && p.max_depth > 0;
+  const unsigned int rpos = warp_append(&S.cnt->r32_count, want_r);
+  const bool r_here = want_r && rpos < kR32InBulk;  // FP64 redo right here
+  unsigned int mine = __ballot_sync(kFull, r_here);
+  while (mine) {
+    const int src = __ffs(mine) - 1;
+    mine &= mine - 1;
+    fp64_element_warp(p, __shfl_sync(kFull, e, src), sm);
+  }
+  if (!act || want_e || r_here) return;
+  const int64_t g = p.base + e;
+  if (outcome == 5) {
+    p.flags[g] = make_flag(kVUndecided, 0, 0);
+    set_status(S.status, kSbIndex);
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    if (p.bmin) p.bmin[g] = nan;
+    if (p.bmax) p.bmax[g] = nan;
+    return;
+  }
+  if (want_r)
+    S.r32[rpos] = e;  // capacity = batch size
+  else  // outcome 2 with a depth cap of 0: undecided at the root
+    p.flags[g] = make_flag(outcome == 0 ? kVInvalid : (outcome == 1 ? kVValid : kVUndecided), 0, 0);
+  if (p.bmin) p.bmin[g] = f2d_int(lo);
+  if (p.bmax) p.bmax[g] = f2d_int(hi);
+}
+
 // This warp's part of the dynamic shared memory of a bulk FP32 kernel.
 __device__ __forceinline__ double* warp_scratch() {
   extern __shared__ double bulk_sm[];
@@ -57,98 +96,6 @@ __global__ void __launch_bounds__(kBulkThreads) bulk64_kernel(Batch p) {
   unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool act = i < static_cast<unsigned int>(p.n);
   fp64_element(p, act, act ? i : 0u);
-}
-
-// ---------------------------------------------------------------- FP32 ----
-// FP64 -> FP32 on the integer pipe, rounding the magnitude to nearest (ties
-// up): |result - x| <= 2^-24 |x|.  Sets `bad` when x is outside the exponent
-// range [2^-126, 2^125) (zero is fine), including NaN and infinities.
-__device__ __forceinline__ float d2f_int(double x, bool& bad) {
-  long long bits = __double_as_longlong(x);
-  uint32_t hi = static_cast<uint32_t>(bits >> 32), lo = static_cast<uint32_t>(bits);
-  uint32_t e = (hi >> 20) & 0x7ffu;
-  bool zero = ((hi << 1) | lo) == 0u;
-  uint32_t f = __funnelshift_l(lo, hi, 3);
-  f = (f & 0x7fffffffu) ^ 0x40000000u;  // exponent field e - 896 for e in [897, 1149]
-  f += (lo >> 28) & 1u;                 // rounding (a carry moves into the exponent)
-  f |= hi & 0x80000000u;
-  bad |= !zero && (e - 897u > 252u);
-  return zero ? __uint_as_float(hi & 0x80000000u) : __uint_as_float(f);
-}
-
-// FP32 -> FP64 on the integer pipe (exact for normal numbers; FP32
-// subnormals, below 2^-126, become signed zeros).
-__device__ __forceinline__ double f2d_int(float v) {
-  uint32_t b = __float_as_uint(v);
-  uint32_t sgn = b & 0x80000000u;
-  bool tiny = (b & 0x7f800000u) == 0u;
-  uint32_t hi = tiny ? sgn : (sgn | (((b & 0x7fffffffu) >> 3) + (896u << 20)));
-  uint32_t lo = tiny ? 0u : (b << 29);
-  return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
-}
-
-__device__ __forceinline__ float fabsmax3(float m, const V3<float>& v) {
-  return fmaxf(m, fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))));
-}
-
-// The FP32 decision of one element from its 8 nodes (FP32): 0 invalid,
-// 1 valid, 3 escalate to FP64; lo / hi = min / max of the 27 coefficients.
-// X bounds |coordinate| (indexed: |node 1| only, completed here with 3 L).
-template <bool INDEXED>
-__device__ __forceinline__ int fp32_decide(const V3<float> Y[8], float X, bool bad, float& lo,
-                                           float& hi) {
-  int outcome;
-  V3<float> a[4], b[4], gg[4];
-  edges_from_nodes(Y, a, b, gg);
-  float L = 0.f;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    L = fabsmax3(L, a[q]);
-    L = fabsmax3(L, b[q]);
-    L = fabsmax3(L, gg[q]);
-  }
-  if (INDEXED) X = fmaf(3.f, L, X);  // every node is within 3 edges of node 1
-  float eps = fmaf(0x1p-24f, L, 0x1p-23f * X);
-  float L2 = L * L;
-  float E = fmaf(256.f * eps, L2, 1024.f * 0x1p-24f * (L2 * L)) * 1.0001f;
-  // too small (underflow) or too large (overflow) for the FP32 bound
-  bad |= !(L >= 0x1p-30f) || !(E < 0x1p100f);
-  if (bad) {
-    outcome = 3;
-  } else {
-    Scaled<float> s;
-    coefficients_from_edges(a, b, gg, s);
-    // per-class minima / maxima (scales 1, 4, 2, 4, 8)
-    float mnC = s.corner[0], mxC = s.corner[0];
-#pragma unroll
-    for (int k = 1; k < 8; ++k) {
-      mnC = fminf(mnC, s.corner[k]);
-      mxC = fmaxf(mxC, s.corner[k]);
-    }
-    float mnS = s.edgeC[0];
-#pragma unroll
-    for (int e = 1; e < 12; ++e) mnS = fminf(mnS, s.edgeC[e]);
-    float mnE = s.edge[0], mxE = s.edge[0];
-#pragma unroll
-    for (int e = 1; e < 12; ++e) {
-      mnE = fminf(mnE, s.edge[e]);
-      mxE = fmaxf(mxE, s.edge[e]);
-    }
-    float mnF = s.face[0], mxF = s.face[0];
-#pragma unroll
-    for (int f = 1; f < 6; ++f) {
-      mnF = fminf(mnF, s.face[f]);
-      mxF = fmaxf(mxF, s.face[f]);
-    }
-    // Step 2: a sample certainly <= 0; Step 4: all 27 certainly > 0
-    bool invalid = (mnC <= -E) | (mnS <= -4.f * E);
-    bool valid = (mnC > E) & (mnS > 4.f * E) & (mnE > 2.f * E) & (mnF > 4.f * E) &
-                 (s.centre > 8.f * E);
-    outcome = invalid ? 0 : (valid ? 1 : 3);
-    lo = fminf(fminf(mnC, mnE * 0.5f), fminf(mnF * 0.25f, s.centre * 0.125f));
-    hi = fmaxf(fmaxf(mxC, mxE * 0.5f), fmaxf(mxF * 0.25f, s.centre * 0.125f));
-  }
-  return outcome;
 }
 
 // Decides what FP32 can decide; everything else is escalated to FP64.
@@ -198,20 +145,7 @@ __global__ void __launch_bounds__(kBulkThreads) bulk32_kernel(Batch p) {
     }
     if (outcome < 0) outcome = fp32_decide<INDEXED>(Y, X, bad, lo, hi);
   }
-  const bool want_e = act && outcome == 3;
-  escalate(p, want_e, i, warp_scratch());
-  if (!act || want_e) return;
-  if (outcome == 5) {
-    p.flags[g] = make_flag(kVUndecided, 0, 0);
-    set_status(S.status, kSbIndex);
-    double nan = __longlong_as_double(0x7ff8000000000000LL);
-    if (p.bmin) p.bmin[g] = nan;
-    if (p.bmax) p.bmax[g] = nan;
-    return;
-  }
-  p.flags[g] = make_flag(outcome == 0 ? kVInvalid : kVValid, 0, 0);
-  if (p.bmin) p.bmin[g] = f2d_int(lo);
-  if (p.bmax) p.bmax[g] = f2d_int(hi);
+  finish32(p, act, outcome, i, lo, hi, warp_scratch());
 }
 
 // Indexed FP32 pass on a persistent grid with its inputs staged through
@@ -304,22 +238,7 @@ __global__ void __launch_bounds__(kBulkThreads, 4) bulk32s_kernel(Batch p) {
     if (act) {
       outcome = ok ? fp32_decide<true>(Y, fabsmax3(0.f, Y[0]), badw != 0.f, lo, hi) : 5;
     }
-    const bool want_e = act && outcome == 3;
-    escalate(p, want_e, e, wsc);
-    if (act && !want_e) {
-      const int64_t g = p.base + static_cast<int64_t>(e);
-      if (outcome == 5) {
-        p.flags[g] = make_flag(kVUndecided, 0, 0);
-        set_status(S.status, kSbIndex);
-        const double nan = __longlong_as_double(0x7ff8000000000000LL);
-        if (p.bmin) p.bmin[g] = nan;
-        if (p.bmax) p.bmax[g] = nan;
-      } else {
-        p.flags[g] = make_flag(outcome == 0 ? kVInvalid : kVValid, 0, 0);
-        if (p.bmin) p.bmin[g] = f2d_int(lo);
-        if (p.bmax) p.bmax[g] = f2d_int(hi);
-      }
-    }
+    finish32(p, act, outcome, e, lo, hi, wsc);
   }
   cp_wait_all();
 }
@@ -340,57 +259,23 @@ int bulk32s_blocks(int threads) {
   return blocks;
 }
 
-// Per-lane decision of the FP32 pass from the scaled coefficients of one
-// lane (0 invalid, 1 valid, 3 escalate) and the lane's min / max.
-struct Lane {
-  float c[8], s[12], e[12], f[6], z;
-};
-__device__ __forceinline__ int decide32(const Lane& q, float E, float& lo, float& hi) {
-  float mnC = q.c[0], mxC = q.c[0];
-#pragma unroll
-  for (int k = 1; k < 8; ++k) {
-    mnC = fminf(mnC, q.c[k]);
-    mxC = fmaxf(mxC, q.c[k]);
-  }
-  float mnS = q.s[0];
-#pragma unroll
-  for (int e = 1; e < 12; ++e) mnS = fminf(mnS, q.s[e]);
-  float mnE = q.e[0], mxE = q.e[0];
-#pragma unroll
-  for (int e = 1; e < 12; ++e) {
-    mnE = fminf(mnE, q.e[e]);
-    mxE = fmaxf(mxE, q.e[e]);
-  }
-  float mnF = q.f[0], mxF = q.f[0];
-#pragma unroll
-  for (int f = 1; f < 6; ++f) {
-    mnF = fminf(mnF, q.f[f]);
-    mxF = fmaxf(mxF, q.f[f]);
-  }
-  bool invalid = (mnC <= -E) | (mnS <= -4.f * E);
-  bool valid = (mnC > E) & (mnS > 4.f * E) & (mnE > 2.f * E) & (mnF > 4.f * E) & (q.z > 8.f * E);
-  lo = fminf(fminf(mnC, mnE * 0.5f), fminf(mnF * 0.25f, q.z * 0.125f));
-  hi = fmaxf(fmaxf(mxC, mxE * 0.5f), fmaxf(mxF * 0.25f, q.z * 0.125f));
-  return invalid ? 0 : (valid ? 1 : 3);
-}
-
 template <int LANE>
 __device__ __forceinline__ float lane(const F2& a) {
   return LANE == 0 ? a.v.x : a.v.y;
 }
 
 template <int LANE>
-__device__ __forceinline__ void lane_of(const Scaled<F2>& s, Lane& q) {
+__device__ __forceinline__ void lane_of(const Scaled<F2>& s, Scaled<float>& q) {
 #pragma unroll
-  for (int k = 0; k < 8; ++k) q.c[k] = lane<LANE>(s.corner[k]);
+  for (int k = 0; k < 8; ++k) q.corner[k] = lane<LANE>(s.corner[k]);
 #pragma unroll
   for (int e = 0; e < 12; ++e) {
-    q.s[e] = lane<LANE>(s.edgeC[e]);
-    q.e[e] = lane<LANE>(s.edge[e]);
+    q.edgeC[e] = lane<LANE>(s.edgeC[e]);
+    q.edge[e] = lane<LANE>(s.edge[e]);
   }
 #pragma unroll
-  for (int f = 0; f < 6; ++f) q.f[f] = lane<LANE>(s.face[f]);
-  q.z = lane<LANE>(s.centre);
+  for (int f = 0; f < 6; ++f) q.face[f] = lane<LANE>(s.face[f]);
+  q.centre = lane<LANE>(s.centre);
 }
 
 // The FP32 pass on two elements per thread (2t and 2t+1) with packed f32x2
@@ -477,51 +362,16 @@ __global__ void __launch_bounds__(kPairThreads) bulk32x2_kernel(Batch p) {
     bad1 |= !(L1 >= 0x1p-30f) || !(E1 < 0x1p100f);
     Scaled<F2> s;
     coefficients_from_edges(a, b, gg, s);
-    Lane q;
+    Scaled<float> q;
     lane_of<0>(s, q);
-    int r0 = decide32(q, E0, lo0, hi0);
+    int r0 = fp32_classify(q, E0, lo0, hi0);
     lane_of<1>(s, q);
-    int r1 = decide32(q, E1, lo1, hi1);
+    int r1 = fp32_classify(q, E1, lo1, hi1);
     if (out0 < 0) out0 = bad0 ? 3 : r0;
     if (out1 < 0) out1 = bad1 ? 3 : r1;
   }
-  const bool e0 = act0 && out0 == 3, e1 = act1 && out1 == 3;
-  escalate(p, e0, i0, warp_scratch());
-  escalate(p, e1, i1, warp_scratch());
-  if (!act0) return;
-  const double nan = __longlong_as_double(0x7ff8000000000000LL);
-  uint8_t f0 = 0, f1 = 0;
-  double l0, h0, l1, h1;
-  auto fin = [&](int out, float lo, float hi, uint8_t& f, double& l, double& h) {
-    if (out == 5) {
-      f = make_flag(kVUndecided, 0, 0);
-      l = h = nan;
-      set_status(S.status, kSbIndex);
-    } else {
-      f = make_flag(out == 0 ? kVInvalid : kVValid, 0, 0);
-      l = f2d_int(lo);
-      h = f2d_int(hi);
-    }
-  };
-  fin(out0, lo0, hi0, f0, l0, h0);
-  if (act1) fin(out1, lo1, hi1, f1, l1, h1);
-  const int64_t g0 = p.base + i0;
-  if (act1 && !e0 && !e1 && (g0 & 1) == 0) {  // both written: paired stores
-    *reinterpret_cast<uchar2*>(p.flags + g0) = make_uchar2(f0, f1);
-    if (p.bmin) *reinterpret_cast<double2*>(p.bmin + g0) = make_double2(l0, l1);
-    if (p.bmax) *reinterpret_cast<double2*>(p.bmax + g0) = make_double2(h0, h1);
-  } else {
-    if (!e0) {
-      p.flags[g0] = f0;
-      if (p.bmin) p.bmin[g0] = l0;
-      if (p.bmax) p.bmax[g0] = h0;
-    }
-    if (act1 && !e1) {
-      p.flags[g0 + 1] = f1;
-      if (p.bmin) p.bmin[g0 + 1] = l1;
-      if (p.bmax) p.bmax[g0 + 1] = h1;
-    }
-  }
+  finish32(p, act0, out0, i0, lo0, hi0, warp_scratch());
+  finish32(p, act1, out1, i1, lo1, hi1, warp_scratch());
 }
 
 // FP64 node -> FP32 record {x, y, z, bad} (16 bytes, one vector load in the

@@ -52,7 +52,10 @@ struct Counters {
   unsigned int arrive;                      // grid barrier of the tail kernel
   unsigned int done;                        // blocks of the tail kernel that finished
   unsigned int amb_count;                   // boxes that sent their element to the exact tier
-  unsigned int pad[10];
+  unsigned int r32_count;                   // FP32 form: elements refined in FP32 (list r32)
+  unsigned int esc2_count;                  // FP32 refinement -> FP64 escalations (list esc2)
+  unsigned int level32_count[kMaxDepth + 2];  // FP32 boxes queued per level
+  unsigned int pad[7];
 };
 
 // Escalations of the FP32 pass: the first kEscInBulk elements appended to
@@ -61,6 +64,12 @@ struct Counters {
 // pass leaves idle); their list entries stay unwritten.  Entries from
 // kEscInBulk on are written and redone by the tail kernel.
 constexpr unsigned int kEscInBulk = 4096;
+
+// Elements the FP32 pass finds to need subdivision: the first kR32InBulk of a
+// batch are redone in FP64 by the pass itself (and refined in FP64: for a
+// handful of elements that is cheaper than the FP32 refinement's own
+// steps), the others are refined in FP32 by the tail kernel (phase R).
+constexpr unsigned int kR32InBulk = 512;
 
 // Counters accumulated across calls (hexval_get_stats).
 struct Stats {
@@ -95,6 +104,19 @@ struct Scratch {
   // prefix sums of the compaction tiles (compact.cu)
   uint64_t* tiles;
   uint64_t tiles_cap;
+  // FP32 form: refinement in FP32 (tail.cu, phase R) of the elements listed
+  // in r32, with its own box queue and per-element state; elements it cannot
+  // settle are listed in esc2 for the FP64 redo
+  uint32_t* r32;
+  uint32_t* esc2;
+  float* q32coef[2];
+  uint32_t* q32slot[2];
+  uint64_t q32cap;
+  uint32_t* s32_elem;
+  uint32_t* s32_state;
+  uint32_t* s32_lev;
+  float* s32_e0;
+  float* s32_m0;
 };
 
 // One batch of elements, as seen by every kernel.

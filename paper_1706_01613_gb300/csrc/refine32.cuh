@@ -1,0 +1,206 @@
+// Refinement in FP32 (FP32-filtered form): the elements the FP32 pass found
+// to need subdivision (all 20 samples certainly positive, a coefficient
+// certainly non-positive) are refined breadth first with FP32 boxes, exactly
+// as the FP64 refinement of tail.cu (Sec. 6: split at 1/2 along xi, eta,
+// zeta by quadratic de Casteljau; a child with a corner certainly <= 0 makes
+// the element INVALID at that level, a child with all 27 certainly > 0 is
+// certified, any other child is queued, or the depth cap is reached).
+// An element whose boxes meet a sign that the FP32 bound cannot settle, or
+// a full queue, is listed in esc2 and redone from scratch in FP64.
+//
+// Error bound of every coefficient at depth d: E0 + d 2^-20 M0, with E0 the
+// FP32 bound of the depth-0 coefficients and M0 >= |every coefficient| (the
+// children are convex combinations; one level adds at most 6 roundings of
+// size 2^-24 M0).
+#pragma once
+
+#include "element32.cuh"
+
+namespace hexval {
+
+__device__ __forceinline__ void split5f(float p0, float p1, float p2, float q[5]) {
+  const float s = p0 + p1, t = p1 + p2;
+  q[0] = p0;
+  q[1] = 0.5f * s;
+  q[2] = 0.25f * (s + t);
+  q[3] = 0.5f * t;
+  q[4] = p2;
+}
+
+// Root box of the i-th element left in the refinement list (list entry
+// kR32InBulk + i; slot i, box i of level 0): the FP32
+// coefficients recomputed exactly as the FP32 pass computed them, with their
+// bound.  Slots beyond the queue capacity are marked for the FP64 redo.
+__device__ __forceinline__ void root32(const Batch& p, bool act, unsigned int i) {
+  if (!act) return;
+  const Scratch& S = p.s;
+  const uint32_t e = ldcg(S.r32 + kR32InBulk + i);
+  V3<float> Y[8];
+  float X, E = 0.f, lo = 0.f, hi = 0.f;
+  bool bad;
+  Scaled<float> s;
+  load_element32(p, p.base + e, Y, X, bad);  // in range: checked by the FP32 pass
+  const bool ok = p.indexed ? fp32_root<true>(Y, X, bad, s, E) : fp32_root<false>(Y, X, bad, s, E);
+  if (ok) fp32_classify(s, E, lo, hi);
+  const bool fits = i < S.q32cap;
+  if (fits) {
+    float A[27];
+    store_tensor(s, A);
+#pragma unroll
+    for (int t = 0; t < 27; ++t) S.q32coef[0][static_cast<uint64_t>(t) * S.q32cap + i] = A[t];
+    S.q32slot[0][i] = i;
+  }
+  S.s32_elem[i] = e;
+  // (ok is always true: the pass formed the same bound)
+  S.s32_state[i] = !fits ? kStOverflow : (ok ? 0u : kStAmbig);
+  S.s32_lev[i] = 0u;
+  S.s32_e0[i] = E;
+  S.s32_m0[i] = fmaxf(fabsf(lo), fabsf(hi)) + E;
+}
+
+// One FP32 box of level `level` (act = false: idle lane).  Called by all lanes.
+__device__ __forceinline__ void refine_box32(const Batch& p, int level, bool act,
+                                             unsigned int idx) {
+  const Scratch& S = p.s;
+  const int in = level & 1, out = in ^ 1;
+  const int child_level = level + 1;
+  const bool last = child_level >= p.max_depth;
+  const uint32_t slot = act ? ldcg(S.q32slot[in] + idx) : 0u;
+  if (act) act = !(ldcg(S.s32_state + slot) & (kStInvalid | kStAmbig | kStOverflow));
+  float G[5][5][5];
+  uint32_t key = 0;
+  if (act) {
+    const float* qc = S.q32coef[in];
+    float A[27];
+#pragma unroll
+    for (int t = 0; t < 27; ++t) A[t] = ldcg(qc + static_cast<uint64_t>(t) * S.q32cap + idx);
+    const float E = fmaf(static_cast<float>(child_level) * 0x1p-20f, ldcg(S.s32_m0 + slot),
+                         ldcg(S.s32_e0 + slot));
+    key = fbits(E);
+    float P1[5][3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        float q[5];
+        split5f(A[tix(0, j, k)], A[tix(1, j, k)], A[tix(2, j, k)], q);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) P1[i][j][k] = q[i];
+      }
+    float P2[5][5][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        float q[5];
+        split5f(P1[i][0][k], P1[i][1][k], P1[i][2][k], q);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) P2[i][j][k] = q[j];
+      }
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+#pragma unroll
+      for (int i = 0; i < 5; ++i) split5f(P2[i][j][0], P2[i][j][1], P2[i][j][2], G[i][j]);
+  }
+  uint32_t bits = 0, queue = 0;
+  if (act) {
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
+      bool nonpos = false, amb = false, notcert = false, amb2 = false;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const Sign3 q = sign_f(G[sx + i][sy + j][sz + k], key);
+            if ((i != 1) && (j != 1) && (k != 1)) {
+              nonpos |= q.nonpos;
+              amb |= !(q.nonpos | q.pos);
+            } else {
+              notcert |= q.nonpos;
+              amb2 |= !(q.nonpos | q.pos);
+            }
+          }
+      if (nonpos) {
+        bits |= kStInvalid;
+      } else if (amb) {
+        bits |= kStAmbig;
+      } else if (notcert) {
+        if (last)
+          bits |= kStCap;
+        else
+          queue |= 1u << o;
+      } else if (amb2) {
+        bits |= kStAmbig;
+      }
+    }
+    if (bits & kStInvalid) queue = 0;  // the element is decided on this level
+  }
+  // one atomic per warp for all the children the warp queues
+  const unsigned int lane = threadIdx.x & 31u;
+  const unsigned int cnt = __popc(queue);
+  unsigned int incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned int v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= static_cast<unsigned int>(d)) incl += v;
+  }
+  const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned int pos = 0;
+  if (total) {
+    if (lane == 31) pos = atomicAdd(&S.cnt->level32_count[child_level], total);
+    pos = __shfl_sync(0xffffffffu, pos, 31) + incl - cnt;
+  }
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    if ((queue >> o) & 1u) {
+      if (pos < S.q32cap) {
+        const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
+        float* dst = S.q32coef[out];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+              dst[static_cast<uint64_t>(tix(i, j, k)) * S.q32cap + pos] = G[sx + i][sy + j][sz + k];
+        S.q32slot[out][pos] = slot;
+      } else {
+        bits |= kStOverflow;
+      }
+      ++pos;
+    }
+  }
+  if (act) {
+    if (bits) atomicOr(&S.s32_state[slot], bits);
+    S.s32_lev[slot] = static_cast<uint32_t>(child_level);
+  }
+}
+
+// Verdict of FP32-refined element `s`, or its listing for the FP64 redo.
+// Called by all lanes.
+__device__ __forceinline__ void finalize32(const Batch& p, bool act, unsigned int s) {
+  const Scratch& S = p.s;
+  const uint32_t st = act ? ldcg(S.s32_state + s) : 0u;
+  const uint32_t lev = act ? ldcg(S.s32_lev + s) : 0u;
+  const uint32_t e = act ? ldcg(S.s32_elem + s) : 0u;
+  const bool redo = act && !(st & kStInvalid) && (st & (kStAmbig | kStOverflow));
+  const unsigned int pos = warp_append(&S.cnt->esc2_count, redo);
+  if (!act) return;
+  if (redo) {
+    S.esc2[pos] = e;  // capacity = batch size
+    return;
+  }
+  uint8_t flag;
+  if (st & kStInvalid)
+    flag = make_flag(kVInvalid, lev, 0);
+  else if (st & kStCap)
+    flag = make_flag(kVUndecided, p.max_depth, 0);
+  else
+    flag = make_flag(kVValid, lev, 0);
+  p.flags[p.base + e] = flag;
+}
+
+}  // namespace hexval

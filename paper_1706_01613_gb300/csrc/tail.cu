@@ -33,6 +33,7 @@
 #include "element64.cuh"
 #include "exact.cuh"
 #include "exact_warp.cuh"
+#include "refine32.cuh"
 #include "warp_items.cuh"
 
 namespace hexval {
@@ -236,13 +237,18 @@ __device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned in
   Stats* st = S.stats;
   unsigned long long boxes = 0, mx = 0;
   for (int l = 1; l <= kMaxDepth + 1; ++l) {
-    unsigned long long c = ldcg(&C->level_count[l]);
-    boxes += c;
+    const unsigned long long c = ldcg(&C->level_count[l]), c32 = ldcg(&C->level32_count[l]);
+    boxes += c + c32;
     mx = c > mx ? c : mx;
+    mx = c32 > mx ? c32 : mx;
   }
   atomicAdd(&st->elements, static_cast<unsigned long long>(p.n));
-  atomicAdd(&st->escalated_fp64, static_cast<unsigned long long>(ldcg(&C->esc_count)));
-  atomicAdd(&st->refined, static_cast<unsigned long long>(ldcg(&C->level_count[0])));
+  const unsigned int nr = ldcg(&C->r32_count);
+  const unsigned int nr_here = nr < kR32InBulk ? nr : kR32InBulk;
+  atomicAdd(&st->escalated_fp64, static_cast<unsigned long long>(ldcg(&C->esc_count)) +
+                                     ldcg(&C->esc2_count) + nr_here);
+  atomicAdd(&st->refined,
+            static_cast<unsigned long long>(ldcg(&C->level_count[0])) + (nr - nr_here));
   atomicAdd(&st->boxes, boxes);
   atomicAdd(&st->exact, static_cast<unsigned long long>(nx));
   atomicMax(&st->max_level_boxes, mx);
@@ -257,7 +263,10 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
   // escalation list entries [kEscInBulk, n_list) are left for this kernel
   const unsigned int n_list = from_list ? ldcg(&C->esc_count) : 0u;
   const unsigned int n_esc = n_list > kEscInBulk ? n_list - kEscInBulk : 0u;
-  if (n_esc == 0 && ldcg(&C->level_count[0]) == 0 && ldcg(&C->exact_count) == 0) {
+  // refinement list entries [kR32InBulk, n_rl) are left for this kernel
+  const unsigned int n_rl = from_list ? ldcg(&C->r32_count) : 0u;
+  const unsigned int n_r = n_rl > kR32InBulk ? n_rl - kR32InBulk : 0u;
+  if (n_esc == 0 && n_r == 0 && ldcg(&C->level_count[0]) == 0 && ldcg(&C->exact_count) == 0) {
     // nothing left: every block reads only counters that are, or become,
     // zero here, so block 0 may end the batch at once
     if (blockIdx.x == 0 && threadIdx.x == 0) fold_stats_and_reset(p, 0u);
@@ -268,12 +277,30 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
   double* mysm = wsm[threadIdx.x >> 5];
   const unsigned int warp_items = kWarpItemsMax * gridDim.x * (blockDim.x >> 5);
   unsigned int epoch = 0;
-  if (n_esc) {  // phase E
+  unsigned int n_esc2 = 0;
+  if (n_r) {  // phase R: refinement in FP32 of the elements listed by the FP32 pass
+    FOR_EACH_ITEM(n_r, i, act) root32(p, act, i);
+    grid_barrier(&C->arrive, epoch, S.status);
+    for (int level = 0; level < p.max_depth; ++level) {
+      const unsigned int n = min(level == 0 ? n_r : ldcg(&C->level32_count[level]),
+                                 static_cast<unsigned int>(S.q32cap));
+      if (n == 0) break;
+      FOR_EACH_ITEM(n, i, act) refine_box32(p, level, act, i);
+      grid_barrier(&C->arrive, epoch, S.status);
+    }
+    FOR_EACH_ITEM(n_r, i, act) finalize32(p, act, i);
+    grid_barrier(&C->arrive, epoch, S.status);
+    n_esc2 = ldcg(&C->esc2_count);
+  }
+  if (n_esc + n_esc2) {  // phase E: list entries, then the FP32 refinement's
     const uint32_t* esc = S.esc + kEscInBulk;
-    if (n_esc <= warp_items) {
-      FOR_EACH_WARP_ITEM(n_esc, i) fp64_element_warp(p, ldcg(esc + i), mysm);
+    const unsigned int n_e = n_esc + n_esc2;
+    if (n_e <= warp_items) {
+      FOR_EACH_WARP_ITEM(n_e, i)
+        fp64_element_warp(p, i < n_esc ? ldcg(esc + i) : ldcg(S.esc2 + (i - n_esc)), mysm);
     } else {
-      FOR_EACH_ITEM(n_esc, i, act) fp64_item(p, act, act ? ldcg(esc + i) : 0u);
+      FOR_EACH_ITEM(n_e, i, act)
+        fp64_item(p, act, act ? (i < n_esc ? ldcg(esc + i) : ldcg(S.esc2 + (i - n_esc))) : 0u);
     }
     grid_barrier(&C->arrive, epoch, S.status);
   }

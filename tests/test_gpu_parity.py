@@ -101,6 +101,21 @@ def test_refinement_heavy(validators, prec):
     assert st["refined"] > 1000 and st["boxes"] > 0
 
 
+def test_fp32_refinement_keeps_most_elements_off_fp64():
+    """Boundary-layer prisms (twist up to 120 degrees, aspect ratio up to
+    1000): most need one refinement level, which the FP32 form does in FP32;
+    flags equal the oracle's and only a minority is redone in FP64."""
+    X = synth.twisted_layers(50_000, seed=4646)
+    v = hv.Validator(precision="fp32", max_depth=10, **CAPS)
+    v.stats(reset=True)
+    got = _run_soa(v, X)
+    st = v.stats()
+    _compare("fp32", got[:3], oracle.check_soa(X, max_depth=10))
+    assert st["refined"] > 5000
+    assert st["escalated_fp64"] < 0.5 * st["refined"], st
+    v.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_depth_caps(prec):
     X = synth.twisted_layers(5000, seed=4545, theta_max_deg=180.0)
