@@ -38,6 +38,7 @@ UNIT = "hex/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+PROFILE_EVERY = 10
 
 
 # ------------------------------------------------------------- workloads ----
@@ -158,17 +159,23 @@ def timed_steps(v, w, dev_in, steps, warmup, flush, profile=False):
     torch.cuda.synchronize()
     v.raise_on_status()
     if profile:
-        v.profile(True)
         v.profile_read(reset=True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     torch.cuda.synchronize()
     wall0 = time.time()
     for i in range(steps):
+        # per-kernel event timing on every PROFILE_EVERY-th step of the timed
+        # region (the events add a few microseconds to the steps they are in)
+        sampled = profile and i % PROFILE_EVERY == 0
+        if sampled:
+            v.profile(True)
         flush.zero_()
         starts[i].record()
         step()
         ends[i].record()
+        if sampled:
+            v.profile(False)
     torch.cuda.synchronize()
     wall1 = time.time()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -385,6 +392,38 @@ def filter_run(steps, warmup, flush):
             "value": n / (ms / 1e3), "unit": "candidate/s", "ms_per_call": ms, "kept": kept}
 
 
+def minj_run(w, dev_in, steps, warmup, flush, rel_tol=1e-6, max_depth=12):
+    """Minimum of J to a tolerance on the benchmark mesh (FP64 branch and
+    bound on the coefficients), per call with CUDA events, L2 flushed."""
+    import torch
+    from paper_1706_01613_gb300 import hexval as hv
+    v = hv.Validator(precision="fp64", max_depth=max_depth)
+
+    def call():
+        if w["kind"] == "indexed":
+            return v.min_jacobian_indexed(dev_in[0], dev_in[1], rel_tol, max_depth)
+        return v.min_jacobian(dev_in[0], rel_tol, max_depth)
+
+    for _ in range(warmup):
+        flush.zero_()
+        call()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        lo, hi, dep = call()
+        b.record()
+    torch.cuda.synchronize()
+    v.raise_on_status()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    d = dep.cpu().numpy()
+    v.close()
+    return {"workload": w["name"], "rel_tol": rel_tol, "max_depth": max_depth,
+            "value": w["n"] / (ms / 1e3), "unit": "hex/s", "ms_per_call": ms,
+            "mean_levels": float((d & 0x7F).mean()), "not_converged": int((d & 0x80).astype(bool).sum())}
+
+
 def serving_run(precision, rate, n_requests, pool, slots=4, budget=40 << 30, seed=20175000):
     """One continuous-batching run: Poisson arrivals at `rate`/s, sizes
     log-uniform in [100, pool size]; returns the latency summary."""
@@ -566,8 +605,10 @@ def main():
 
     quads = quad_run(max(5, args.steps // 20), 3, flush) if args.quads else None
     filt = filter_run(max(5, args.steps // 50), 3, flush) if args.quads else None
+    mj = minj_run(w, dev_in, 5, 2, flush) if args.quads else None
 
-    launches_per_step = sum(v[1] for v in phases.values()) / args.steps
+    sampled_steps = (args.steps + PROFILE_EVERY - 1) // PROFILE_EVERY
+    launches_per_step = sum(v[1] for v in phases.values()) / sampled_steps
     rec = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -592,6 +633,7 @@ def main():
         "latency": latency,
         "quads": quads,
         "filter": filt,
+        "min_jacobian": mj,
         "clocks": clocks.summary(*window),
     }
     print(json.dumps(rec))

@@ -192,6 +192,32 @@ int hexval_corner_quality_indexed(hexval_handle h, int64_t n_nodes, const double
 int hexval_compact(hexval_handle h, int64_t n, const uint8_t* flags, uint32_t verdict_mask,
                    int32_t* ids, int32_t* count, void* stream);
 
+/* Minimum of the Jacobian determinant to a tolerance (Sec. 1 and Sec. 3:
+ * the smallest Bezier coefficient of a box bounds J from below on it, its
+ * smallest corner coefficient bounds the minimum from above, and
+ * subdividing sharpens both).  Per element, breadth first: boxes whose lower
+ * bound is below U - tol are split in 8, until U - L <= tol with
+ * tol = rel_tol * max |b| (b the 27 depth-0 coefficients) or max_depth
+ * levels; every value carries a certified FP64 error bound, so the true
+ * minimum of J over the reference cube lies in [jmin_lo, jmin_hi].
+ *
+ * corners: as for hexval_check_soa.  jmin_lo, jmin_hi: device, n_hex
+ * doubles (NaN for non-finite input).  depth: device, n_hex bytes, the levels
+ * used, bit 7 set when the tolerance was not reached (depth cap, or more
+ * boxes on a level than the element's share of the handle's queue).
+ * 0 <= max_depth <= 15, rel_tol >= 0.  Stream-ordered, no allocation (the
+ * boxes live in the handle's refinement queue); errors as hexval_check_soa. */
+int hexval_min_jacobian(hexval_handle h, int64_t n_hex, const double* corners, double rel_tol,
+                        int32_t max_depth, double* jmin_lo, double* jmin_hi, uint8_t* depth,
+                        void* stream);
+
+/* The same on an indexed mesh (nodes [n_nodes][3] FP64, conn [n_hex][8]
+ * int32); an out-of-range entry gives NaN bounds and HEXVAL_E_INDEX. */
+int hexval_min_jacobian_indexed(hexval_handle h, int64_t n_nodes, const double* nodes,
+                                int64_t n_hex, const int32_t* conn, double rel_tol,
+                                int32_t max_depth, double* jmin_lo, double* jmin_hi,
+                                uint8_t* depth, void* stream);
+
 /* Synchronises the stream, returns the sticky device status (HEXVAL_OK or
  * the most severe device-detected code) and clears it. */
 int hexval_status(hexval_handle h, void* stream);

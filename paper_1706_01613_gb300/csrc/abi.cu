@@ -355,6 +355,49 @@ int hexval_compact(hexval_handle h, int64_t n, const uint8_t* flags, uint32_t ve
              : HEXVAL_E_CUDA;
 }
 
+int hexval_min_jacobian(hexval_handle h, int64_t n_hex, const double* corners, double rel_tol,
+                        int32_t max_depth, double* jmin_lo, double* jmin_hi, uint8_t* depth,
+                        void* stream) {
+  if (!h || n_hex < 0 || n_hex >= (1ll << 31) || !(rel_tol >= 0.0) || max_depth < 0 ||
+      max_depth > hexval::kMaxDepth)
+    return HEXVAL_E_ARG;
+  if (n_hex == 0) return HEXVAL_OK;
+  if (!corners || !jmin_lo || !jmin_hi || !depth) return HEXVAL_E_ARG;
+  if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;
+  Batch p{};
+  p.n = n_hex;
+  p.soa = corners;
+  p.stride = n_hex;
+  p.s = h->s;
+  return hexval::launch_minj(p, rel_tol, max_depth, jmin_lo, jmin_hi, depth, &h->s.cnt->minj_next,
+                             static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? HEXVAL_OK
+             : HEXVAL_E_CUDA;
+}
+
+int hexval_min_jacobian_indexed(hexval_handle h, int64_t n_nodes, const double* nodes,
+                                int64_t n_hex, const int32_t* conn, double rel_tol,
+                                int32_t max_depth, double* jmin_lo, double* jmin_hi,
+                                uint8_t* depth, void* stream) {
+  if (!h || n_hex < 0 || n_hex >= (1ll << 31) || n_nodes < 0 || n_nodes >= (1ll << 31) ||
+      !(rel_tol >= 0.0) || max_depth < 0 || max_depth > hexval::kMaxDepth)
+    return HEXVAL_E_ARG;
+  if (n_hex == 0) return HEXVAL_OK;
+  if (!nodes || !conn || !jmin_lo || !jmin_hi || !depth || n_nodes == 0) return HEXVAL_E_ARG;
+  if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;
+  Batch p{};
+  p.n = n_hex;
+  p.nodes = nodes;
+  p.n_nodes = n_nodes;
+  p.conn = conn;
+  p.indexed = 1;
+  p.s = h->s;
+  return hexval::launch_minj(p, rel_tol, max_depth, jmin_lo, jmin_hi, depth, &h->s.cnt->minj_next,
+                             static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? HEXVAL_OK
+             : HEXVAL_E_CUDA;
+}
+
 int hexval_status(hexval_handle h, void* stream) {
   if (!h) return HEXVAL_E_ARG;
   if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;

@@ -34,6 +34,7 @@ constexpr int kBulk32Default = 128;  // default block of the FP32 kernels (measu
 // one at a time by the whole warp, on `sm` (kElemScratch doubles of shared
 // memory per warp); the others are written to the list for the tail kernel.
 __device__ __forceinline__ void escalate(const Batch& p, bool want, unsigned int e, double* sm) {
+  if (!__any_sync(kFull, want)) return;
   const unsigned int pos = warp_append(&p.s.cnt->esc_count, want);
   if (want && pos >= kEscInBulk) p.s.esc[pos] = e;  // capacity = batch size
   unsigned int mine = __ballot_sync(kFull, want && pos < kEscInBulk);
@@ -56,13 +57,17 @@ __device__ __forceinline__ void finish32(const Batch& p, bool act, int outcome, 
   const bool want_e = act && outcome == 3;
   escalate(p, want_e, e, sm);
   const bool want_r = act && outcome == 2 && p.max_depth > 0;
-  const unsigned int rpos = warp_append(&S.cnt->r32_count, want_r);
-  const bool r_here = want_r && rpos < kR32InBulk;  // FP64 redo right here
-  unsigned int mine = __ballot_sync(kFull, r_here);
-  while (mine) {
-    const int src = __ffs(mine) - 1;
-    mine &= mine - 1;
-    fp64_element_warp(p, __shfl_sync(kFull, e, src), sm);
+  unsigned int rpos = 0;
+  bool r_here = false;
+  if (__any_sync(kFull, want_r)) {  // rare: skip the list work otherwise
+    rpos = warp_append(&S.cnt->r32_count, want_r);
+    r_here = want_r && rpos < kR32InBulk;  // FP64 redo right here
+    unsigned int mine = __ballot_sync(kFull, r_here);
+    while (mine) {
+      const int src = __ffs(mine) - 1;
+      mine &= mine - 1;
+      fp64_element_warp(p, __shfl_sync(kFull, e, src), sm);
+    }
   }
   if (!act || want_e || r_here) return;
   const int64_t g = p.base + e;

@@ -55,7 +55,8 @@ struct Counters {
   unsigned int r32_count;                   // FP32 form: elements refined in FP32 (list r32)
   unsigned int esc2_count;                  // FP32 refinement -> FP64 escalations (list esc2)
   unsigned int level32_count[kMaxDepth + 2];  // FP32 boxes queued per level
-  unsigned int pad[7];
+  unsigned int minj_next;                   // element counter of the minimum-of-J kernel
+  unsigned int pad[6];
 };
 
 // Escalations of the FP32 pass: the first kEscInBulk elements appended to
@@ -566,6 +567,8 @@ cudaError_t launch_nodes32(const Batch& p, cudaStream_t st);
 cudaError_t launch_tail(const Batch& p, bool from_list, cudaStream_t st);
 cudaError_t launch_quads(const QuadBatch& p, bool fp32, cudaStream_t st);
 cudaError_t launch_quality(const Batch& p, float* sj, cudaStream_t st);
+cudaError_t launch_minj(const Batch& p, double rel_tol, int max_depth, double* lo, double* hi,
+                        uint8_t* depth, unsigned int* counter, cudaStream_t st);
 int64_t compact_tiles(int64_t n);
 cudaError_t launch_compact(const uint8_t* flags, int64_t n, uint32_t mask, uint64_t* tiles,
                            int32_t* ids, int32_t* count, cudaStream_t st);

@@ -83,12 +83,17 @@ __device__ __forceinline__ void sample_columns(int t, int& A, int& B, int& C) {
   }
 }
 
-// Warp-cooperative fp64_element (element64.cuh): element e of the batch,
-// all 32 lanes, `sm` = this warp's shared scratch.
-static __device__ __noinline__ void fp64_element_warp(const Batch& p, uint32_t e, double* sm) {
-  const Scratch& S = p.s;
+// The 20 samples and 27 scaled coefficients of element g in FP64 by the
+// whole warp (all 32 lanes), on `sm` (kElemScratch doubles): lane t < 20
+// gets sample t (smp, scaled as in Scaled<>), lane L < 27 the scaled
+// coefficient of class slot L (coef: 0-7 corners, 8-19 edges (2 b), 20-25
+// faces (4 b), 26 centre (8 b)), and every lane the bound E of the unscaled
+// coefficients (2^(3 e_L - 3107) >= 2^-42 L^3, as element64.cuh).  Returns
+// 0, or 1 for a connectivity entry out of range, 2 for a non-finite
+// coordinate (nothing else is then computed).
+__device__ __forceinline__ int warp_root64(const Batch& p, int64_t g, double* sm, double& smp,
+                                           double& coef, double& E) {
   const int lane = threadIdx.x & 31;
-  const int64_t g = p.base + e;
   double* Xs = sm;           // 24 coordinates [node][d]
   double* V = sm + 24;       // 24 vectors x 3 (0-11 edges, 12-23 sums)
   double* Sm = sm + 96;      // 20 samples (scaled as in Scaled<>)
@@ -103,25 +108,8 @@ static __device__ __noinline__ void fp64_element_warp(const Batch& p, uint32_t e
     if (!bad && lane < 24) Xs[lane] = __ldg(p.nodes + 3 * static_cast<int64_t>(nid) + lane % 3);
   }
   __syncwarp();
-  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
-  if (bad) {
-    if (lane == 0) {
-      p.flags[g] = make_flag(kVUndecided, 0, 0);
-      if (p.bmin) p.bmin[g] = qnan;
-      if (p.bmax) p.bmax[g] = qnan;
-      set_status(S.status, kSbIndex);
-    }
-    return;
-  }
-  bool nonfin = __any_sync(kFull, lane < 24 && (dhi(Xs[lane]) & 0x7ff00000u) == 0x7ff00000u);
-  if (nonfin) {
-    if (lane == 0) {
-      p.flags[g] = make_flag(kVNonfinite, 0, 0);
-      if (p.bmin) p.bmin[g] = qnan;
-      if (p.bmax) p.bmax[g] = qnan;
-    }
-    return;
-  }
+  if (bad) return 1;
+  if (__any_sync(kFull, lane < 24 && (dhi(Xs[lane]) & 0x7ff00000u) == 0x7ff00000u)) return 2;
   // 12 edge vectors (36 components) and the bound's exponent
   uint32_t m = 0;
 #pragma unroll
@@ -149,7 +137,7 @@ static __device__ __noinline__ void fp64_element_warp(const Batch& p, uint32_t e
   }
   __syncwarp();
   // 20 samples: lane t computes det of its three columns
-  double smp = 0.0;
+  smp = 0.0;
   if (lane < 20) {
     int A, B, C;
     sample_columns(lane, A, B, C);
@@ -161,7 +149,7 @@ static __device__ __noinline__ void fp64_element_warp(const Batch& p, uint32_t e
   }
   __syncwarp();
   // scaled Table t:Tsmall (same expressions as coefficients_from_edges)
-  double coef = 0.0;  // lanes 0-7 corners, 8-19 edges (2b), 20-25 faces (4b), 26 centre (8b)
+  coef = 0.0;  // lanes 0-7 corners, 8-19 edges (2b), 20-25 faces (4b), 26 centre (8b)
   if (lane < 8) {
     coef = smp;
   } else if (lane < 20) {
@@ -195,9 +183,30 @@ static __device__ __noinline__ void fp64_element_warp(const Batch& p, uint32_t e
     double esum = (ez0 + ez1) + ((C[8] + C[9]) + (C[10] + C[11]));
     coef = fma(-5.0, cz0 + cz1, esum);
   }
-  // certified classification (element64.cuh: classify_root)
   const int emax = static_cast<int>(m >> 20);
-  const double E = pow2d(min(3 * emax - 3107, 1000));
+  E = pow2d(min(3 * emax - 3107, 1000));
+  return 0;
+}
+
+// Warp-cooperative fp64_element (element64.cuh): element e of the batch,
+// all 32 lanes, `sm` = this warp's shared scratch.
+static __device__ __noinline__ void fp64_element_warp(const Batch& p, uint32_t e, double* sm) {
+  const Scratch& S = p.s;
+  const int lane = threadIdx.x & 31;
+  const int64_t g = p.base + e;
+  double smp, coef, E;
+  const int rc = warp_root64(p, g, sm, smp, coef, E);
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+  if (rc) {
+    if (lane == 0) {
+      p.flags[g] = make_flag(rc == 1 ? kVUndecided : kVNonfinite, 0, 0);
+      if (p.bmin) p.bmin[g] = qnan;
+      if (p.bmax) p.bmax[g] = qnan;
+      if (rc == 1) set_status(S.status, kSbIndex);
+    }
+    return;
+  }
+  // certified classification (element64.cuh: classify_root)
   const uint32_t k1 = dhi(E);
   // sample keys: corners k1, edge samples x4; coefficient keys: edges x2,
   // faces x4, centre x8

@@ -29,7 +29,8 @@ EXPORTS = ("hexval_config_default", "hexval_create", "hexval_destroy", "hexval_c
            "hexval_check_indexed", "hexval_status", "hexval_get_stats", "hexval_profile_enable",
            "hexval_profile_read", "hexval_check_soa_noalloc", "hexval_check_quads",
            "hexval_check_quads_indexed", "hexval_corner_quality",
-           "hexval_corner_quality_indexed", "hexval_compact", "hexval_strerror")
+           "hexval_corner_quality_indexed", "hexval_compact", "hexval_min_jacobian",
+           "hexval_min_jacobian_indexed", "hexval_strerror")
 PHASES = ("nodes32", "bulk32", "bulk64", "tail", "exact", "-", "-", "-")
 
 
@@ -93,6 +94,10 @@ def load(build_if_missing=False):
     lib.hexval_corner_quality.argtypes = [vp, i64, vp, vp, vp]
     lib.hexval_corner_quality_indexed.argtypes = [vp, i64, vp, i64, vp, vp, vp]
     lib.hexval_compact.argtypes = [vp, i64, vp, ctypes.c_uint32, vp, vp, vp]
+    f64 = ctypes.c_double
+    lib.hexval_min_jacobian.argtypes = [vp, i64, vp, f64, ctypes.c_int32, vp, vp, vp, vp]
+    lib.hexval_min_jacobian_indexed.argtypes = [vp, i64, vp, i64, vp, f64, ctypes.c_int32, vp,
+                                                vp, vp, vp]
     lib.hexval_strerror.argtypes = [ctypes.c_int]
     lib.hexval_strerror.restype = ctypes.c_char_p
     _lib = lib
@@ -301,6 +306,42 @@ class Validator:
         if stream is not None:
             stream.synchronize()
         return ids[:int(count.item())]
+
+    def min_jacobian(self, corners, rel_tol=1e-6, max_depth=12, stream=None):
+        """Certified bounds (lo, hi) of the minimum of J of each element
+        (corners as for check_soa) and the levels used (uint8, bit 7 = the
+        tolerance was not reached)."""
+        import torch
+        if corners.dtype != torch.float64 or not corners.is_cuda or not corners.is_contiguous():
+            raise ValueError("corners must be a contiguous float64 CUDA tensor (8, 3, n)")
+        if corners.dim() != 3 or tuple(corners.shape[:2]) != (8, 3):
+            raise ValueError("corners must have shape (8, 3, n)")
+        n = corners.shape[2]
+        lo = torch.empty(n, dtype=torch.float64, device=corners.device)
+        hi = torch.empty_like(lo)
+        depth = torch.empty(n, dtype=torch.uint8, device=corners.device)
+        rc = self._lib.hexval_min_jacobian(self._h, n, self._ptr(corners), float(rel_tol),
+                                           int(max_depth), self._ptr(lo), self._ptr(hi),
+                                           self._ptr(depth), _stream_ptr(stream))
+        _check(rc, "hexval_min_jacobian")
+        return lo, hi, depth
+
+    def min_jacobian_indexed(self, nodes, conn, rel_tol=1e-6, max_depth=12, stream=None):
+        """As min_jacobian on an indexed mesh."""
+        import torch
+        if nodes.dtype != torch.float64 or conn.dtype != torch.int32 or not nodes.is_cuda \
+                or not conn.is_cuda or not nodes.is_contiguous() or not conn.is_contiguous():
+            raise ValueError("nodes: contiguous float64 CUDA (n_nodes, 3); conn: int32 (n, 8)")
+        n = conn.shape[0]
+        lo = torch.empty(n, dtype=torch.float64, device=nodes.device)
+        hi = torch.empty_like(lo)
+        depth = torch.empty(n, dtype=torch.uint8, device=nodes.device)
+        rc = self._lib.hexval_min_jacobian_indexed(self._h, nodes.shape[0], self._ptr(nodes), n,
+                                                   self._ptr(conn), float(rel_tol),
+                                                   int(max_depth), self._ptr(lo), self._ptr(hi),
+                                                   self._ptr(depth), _stream_ptr(stream))
+        _check(rc, "hexval_min_jacobian_indexed")
+        return lo, hi, depth
 
     def check_host(self, kind, *arrays, stream=None):
         """End-to-end call on host data: copies the inputs (pinned host
