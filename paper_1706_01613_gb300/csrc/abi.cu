@@ -176,7 +176,8 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
          alloc(h, &s.q32slot[0], s.q32cap) && alloc(h, &s.q32slot[1], s.q32cap) &&
          alloc(h, &s.s32_elem, cfg->max_batch) && alloc(h, &s.s32_state, cfg->max_batch) &&
          alloc(h, &s.s32_lev, cfg->max_batch) && alloc(h, &s.s32_e0, cfg->max_batch) &&
-         alloc(h, &s.s32_m0, cfg->max_batch);
+         alloc(h, &s.s32_m0, cfg->max_batch) &&
+         alloc(h, &s.iw, static_cast<uint64_t>(hexval::kIwSlots) * 2 * 27 * hexval::kIwBoxes);
   }
   if (!ok) {
     free_all(h);

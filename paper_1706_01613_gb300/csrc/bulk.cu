@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kBulkThreads) bulk64_kernel(Batch p) {
 
 // Decides what FP32 can decide; everything else is escalated to FP64.
 template <bool INDEXED>
-__global__ void __launch_bounds__(kBulkThreads) bulk32_kernel(Batch p) {
+__global__ void __launch_bounds__(kBulkThreads, 4) bulk32_kernel(Batch p) {
   const Scratch& S = p.s;
   unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool act = i < static_cast<unsigned int>(p.n);
@@ -288,7 +288,7 @@ __device__ __forceinline__ void lane_of(const Scaled<F2>& s, Scaled<float>& q) {
 constexpr int kPairThreads = 128;
 
 template <bool INDEXED>
-__global__ void __launch_bounds__(kPairThreads) bulk32x2_kernel(Batch p) {
+__global__ void __launch_bounds__(kPairThreads, 4) bulk32x2_kernel(Batch p) {
   const Scratch& S = p.s;
   const unsigned int t = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned int i0 = 2 * t, i1 = 2 * t + 1;

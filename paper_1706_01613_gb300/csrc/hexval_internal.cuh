@@ -56,7 +56,9 @@ struct Counters {
   unsigned int esc2_count;                  // FP32 refinement -> FP64 escalations (list esc2)
   unsigned int level32_count[kMaxDepth + 2];  // FP32 boxes queued per level
   unsigned int minj_next;                   // element counter of the minimum-of-J kernel
-  unsigned int pad[6];
+  unsigned int iw_count;                    // in-warp refinement workspaces taken
+  unsigned int iw_done;                     // elements decided by the in-warp refinement
+  unsigned int pad[4];
 };
 
 // Escalations of the FP32 pass: the first kEscInBulk elements appended to
@@ -71,6 +73,11 @@ constexpr unsigned int kEscInBulk = 4096;
 // handful of elements that is cheaper than the FP32 refinement's own
 // steps), the others are refined in FP32 by the tail kernel (phase R).
 constexpr unsigned int kR32InBulk = 512;
+
+// In-warp FP64 refinement (warp_items.cuh): workspaces per batch and boxes
+// per level of one workspace.
+constexpr unsigned int kIwSlots = 64;
+constexpr unsigned int kIwBoxes = 64;
 
 // Counters accumulated across calls (hexval_get_stats).
 struct Stats {
@@ -118,6 +125,8 @@ struct Scratch {
   uint32_t* s32_lev;
   float* s32_e0;
   float* s32_m0;
+  // FP32 form: workspaces of the in-warp FP64 refinement (warp_items.cuh)
+  double* iw;
 };
 
 // One batch of elements, as seen by every kernel.

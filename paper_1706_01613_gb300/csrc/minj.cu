@@ -60,13 +60,6 @@ __device__ __forceinline__ double warp_max_abs(double v) {
   return __longlong_as_double(static_cast<long long>(k));
 }
 
-__device__ __forceinline__ int tensor_pos(int lane) {
-  if (lane < 8) return corner_t(lane);
-  if (lane < 20) return edge_t(lane - 8);
-  if (lane < 26) return face_t(lane - 20);
-  return tix(1, 1, 1);
-}
-
 __global__ void __launch_bounds__(kMinjThreads) minj_kernel(Batch p, MinjArgs a) {
   __shared__ double wsm[kMinjThreads / 32][kWarpScratch];
   double* sm = wsm[threadIdx.x >> 5];

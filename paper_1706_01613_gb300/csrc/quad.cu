@@ -229,14 +229,7 @@ __device__ __forceinline__ double quad_f2d(float v) {
 // exact one (L >= |computed difference|); a corner value is then within
 // 4 eps (L + eps) + 2 eps^2 of its exact value from the inputs and within
 // 4 u (L + eps)^2 (u = 2^-24) from its own roundings.
-__global__ void __launch_bounds__(kQuadThreads, 4) quad32_kernel(QuadBatch p) {
-  const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (g >= p.n) return;
-  Quad64 q;
-  if (!quad_load(p, g, q)) {
-    quad_bad_index(p, g);
-    return;
-  }
+__device__ __forceinline__ void quad32_decide(const Quad64& q, const QuadBatch& p, int64_t g) {
   bool bad = false;
   float x[4], y[4], X = 0.f;
 #pragma unroll
@@ -266,15 +259,36 @@ __global__ void __launch_bounds__(kQuadThreads, 4) quad32_kernel(QuadBatch p) {
   quad_fp64(q, p, g);  // escalation
 }
 
+// Two quadrangles per thread, i and i + ceil(n/2), loaded before either is
+// computed: twice the loads in flight per thread (the gather of the node
+// coordinates is latency-bound).
+__global__ void __launch_bounds__(kQuadThreads, 4) quad32_kernel(QuadBatch p) {
+  const int64_t half = (p.n + 1) / 2;
+  const int64_t g0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (g0 >= half) return;
+  const int64_t g1 = g0 + half;
+  const bool two = g1 < p.n;
+  Quad64 q0, q1;
+  const bool ok0 = quad_load(p, g0, q0);
+  const bool ok1 = two && quad_load(p, g1, q1);
+  if (ok0) quad32_decide(q0, p, g0); else quad_bad_index(p, g0);
+  if (two) {
+    if (ok1) quad32_decide(q1, p, g1); else quad_bad_index(p, g1);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_quads(const QuadBatch& p, bool fp32, cudaStream_t st) {
   if (p.n <= 0) return cudaSuccess;
-  const unsigned int blocks = static_cast<unsigned int>((p.n + kQuadThreads - 1) / kQuadThreads);
-  if (fp32)
-    quad32_kernel<<<blocks, kQuadThreads, 0, st>>>(p);
-  else
-    quad64_kernel<<<blocks, kQuadThreads, 0, st>>>(p);
+  if (fp32) {
+    const int64_t half = (p.n + 1) / 2;
+    quad32_kernel<<<static_cast<unsigned int>((half + kQuadThreads - 1) / kQuadThreads),
+                    kQuadThreads, 0, st>>>(p);
+  } else {
+    quad64_kernel<<<static_cast<unsigned int>((p.n + kQuadThreads - 1) / kQuadThreads),
+                    kQuadThreads, 0, st>>>(p);
+  }
   return cudaGetLastError();
 }
 

@@ -247,8 +247,8 @@ __device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned in
   const unsigned int nr_here = nr < kR32InBulk ? nr : kR32InBulk;
   atomicAdd(&st->escalated_fp64, static_cast<unsigned long long>(ldcg(&C->esc_count)) +
                                      ldcg(&C->esc2_count) + nr_here);
-  atomicAdd(&st->refined,
-            static_cast<unsigned long long>(ldcg(&C->level_count[0])) + (nr - nr_here));
+  atomicAdd(&st->refined, static_cast<unsigned long long>(ldcg(&C->level_count[0])) +
+                              (nr - nr_here) + ldcg(&C->iw_done));
   atomicAdd(&st->boxes, boxes);
   atomicAdd(&st->exact, static_cast<unsigned long long>(nx));
   atomicMax(&st->max_level_boxes, mx);

@@ -19,7 +19,9 @@
 namespace hexval {
 
 constexpr int kWarpScratch = 272;  // doubles per warp (box: 27 + 45 + 75 + 125)
-constexpr int kElemScratch = 116;  // doubles per warp used by fp64_element_warp
+// doubles per warp that fp64_element_warp needs: 116 for the element itself,
+// the full kWarpScratch when it refines the element in-warp (refine_in_warp)
+constexpr int kElemScratch = kWarpScratch;
 constexpr unsigned int kFull = 0xffffffffu;
 
 __device__ __forceinline__ double shfl_d(double v, int src) {
@@ -84,7 +86,7 @@ __device__ __forceinline__ void sample_columns(int t, int& A, int& B, int& C) {
 }
 
 // The 20 samples and 27 scaled coefficients of element g in FP64 by the
-// whole warp (all 32 lanes), on `sm` (kElemScratch doubles): lane t < 20
+// whole warp (all 32 lanes), on `sm` (116 doubles): lane t < 20
 // gets sample t (smp, scaled as in Scaled<>), lane L < 27 the scaled
 // coefficient of class slot L (coef: 0-7 corners, 8-19 edges (2 b), 20-25
 // faces (4 b), 26 centre (8 b)), and every lane the bound E of the unscaled
@@ -188,6 +190,148 @@ __device__ __forceinline__ int warp_root64(const Batch& p, int64_t g, double* sm
   return 0;
 }
 
+// Tensor position of the coefficient held by class slot `lane` (0-26).
+__device__ __forceinline__ int tensor_pos(int lane) {
+  if (lane < 8) return corner_t(lane);
+  if (lane < 20) return edge_t(lane - 8);
+  if (lane < 26) return face_t(lane - 20);
+  return tix(1, 1, 1);
+}
+
+__device__ __forceinline__ void split5_row(const double* in, int stride_in, double* out,
+                                           int stride_out) {
+  double p0 = in[0], p1 = in[stride_in], p2 = in[2 * stride_in];
+  double s = p0 + p1, t = p1 + p2;
+  out[0] = p0;
+  out[stride_out] = 0.5 * s;
+  out[2 * stride_out] = 0.25 * (s + t);
+  out[3 * stride_out] = 0.5 * t;
+  out[4 * stride_out] = p2;
+}
+
+// The three de Casteljau passes of a box whose 27 coefficients are in
+// sm[0..27) (tensor order): its 125 split values into sm[147..272), indexed
+// (i + 5 (j + 5 k)).  All lanes.
+__device__ __forceinline__ void split_box_warp(double* sm) {
+  const int lane = threadIdx.x & 31;
+  double* A = sm;        // [i + 3 j + 9 k]
+  double* P1 = sm + 27;  // [i + 5 (j + 3 k)], i < 5
+  double* P2 = sm + 72;  // [i + 5 (j + 5 k)], i, j < 5
+  double* G = sm + 147;  // [i + 5 (j + 5 k)], i, j, k < 5
+  __syncwarp();
+  if (lane < 9) {  // along xi: row (j, k)
+    int j = lane % 3, k = lane / 3;
+    split5_row(A + 3 * j + 9 * k, 1, P1 + 5 * (j + 3 * k), 1);
+  }
+  __syncwarp();
+  if (lane < 15) {  // along eta: row (i, k)
+    int i = lane % 5, k = lane / 5;
+    split5_row(P1 + i + 15 * k, 5, P2 + i + 25 * k, 5);
+  }
+  __syncwarp();
+  if (lane < 25) {  // along zeta: row (i, j)
+    int i = lane % 5, j = lane / 5;
+    split5_row(P2 + i + 5 * j, 25, G + i + 5 * j, 25);
+  }
+  __syncwarp();
+}
+
+// Classification of child `o` (lane o < 8) of a split box against the bound
+// key: the state bits it contributes and whether it must be queued (as
+// refine_box in tail.cu).
+__device__ __forceinline__ void classify_child_warp(const double* G, uint32_t key, bool last,
+                                                    uint32_t& bits, bool& want) {
+  const int lane = threadIdx.x & 31;
+  bits = 0;
+  want = false;
+  if (lane >= 8) return;
+  const int sx = 2 * (lane & 1), sy = 2 * ((lane >> 1) & 1), sz = 2 * (lane >> 2);
+  bool nonpos = false, amb = false, notcert = false, amb2 = false;
+  for (int k = 0; k < 3; ++k)
+    for (int j = 0; j < 3; ++j)
+      for (int i = 0; i < 3; ++i) {
+        Sign3 q = sign_d(G[(sx + i) + 5 * ((sy + j) + 5 * (sz + k))], key);
+        if ((i != 1) && (j != 1) && (k != 1)) {
+          nonpos |= q.nonpos;
+          amb |= !(q.nonpos | q.pos);
+        } else {
+          notcert |= q.nonpos;
+          amb2 |= !(q.nonpos | q.pos);
+        }
+      }
+  if (nonpos) bits = kStInvalid;
+  else if (amb) bits = kStAmbig;
+  else if (notcert) { if (last) bits = kStCap; else want = true; }
+  else if (amb2) bits = kStAmbig;
+}
+
+// In-warp refinement (FP32-filtered form): a few elements a batch need
+// subdivision after their FP64 redo; the warp that redid one refines it at
+// once, breadth first in a workspace of its own, with the same arithmetic,
+// bounds and order-free verdict as the refinement of tail.cu, instead of
+// queueing it for the tail kernel.  Returns the flag byte, or -1 when the
+// element must go to the tail's refinement after all (no workspace left, a
+// level of more than kIwBoxes boxes, or a sign FP64 cannot settle).  `un` =
+// this lane's unscaled root coefficient (class slot lane < 27).
+static __device__ __noinline__ int refine_in_warp(const Batch& p, double un, double E0, double M0,
+                                                  double* sm) {
+  const Scratch& S = p.s;
+  const int lane = threadIdx.x & 31;
+  if (!S.iw) return -1;
+  unsigned int slot = 0;
+  if (lane == 0) slot = atomicAdd(&S.cnt->iw_count, 1u);
+  slot = __shfl_sync(kFull, slot, 0);
+  if (slot >= kIwSlots) return -1;
+  double* W = S.iw + static_cast<uint64_t>(slot) * 2 * 27 * kIwBoxes;  // [buf][t][box]
+  if (lane < 27) W[static_cast<uint64_t>(tensor_pos(lane)) * kIwBoxes] = un;
+  __syncwarp();
+  unsigned int nb = 1;
+  int cur = 0;
+  const double* G = sm + 147;
+  for (int level = 0; level < p.max_depth; ++level) {
+    const int child_level = level + 1;
+    const bool last = child_level >= p.max_depth;
+    const double E = fma(static_cast<double>(child_level) * 0x1p-49, M0, E0);
+    const uint32_t key = dhi(E);
+    uint32_t bits = 0;
+    unsigned int nn = 0;
+    const double* in = W + static_cast<uint64_t>(cur) * 27 * kIwBoxes;
+    double* out = W + static_cast<uint64_t>(cur ^ 1) * 27 * kIwBoxes;
+    for (unsigned int j = 0; j < nb && !(bits & kStInvalid); ++j) {
+      if (lane < 27) sm[lane] = in[static_cast<uint64_t>(lane) * kIwBoxes + j];
+      split_box_warp(sm);
+      uint32_t cbits;
+      bool want;
+      classify_child_warp(G, key, last, cbits, want);
+      bits |= __reduce_or_sync(kFull, cbits);
+      const uint32_t queue = (bits & kStInvalid) ? 0u : (__ballot_sync(kFull, want) & 0xffu);
+      for (uint32_t q = queue; q; q &= q - 1) {
+        const int o = __ffs(q) - 1;
+        if (nn < kIwBoxes) {
+          const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
+          if (lane < 27) {
+            const int i = lane % 3, jj = (lane / 3) % 3, k = lane / 9;
+            out[static_cast<uint64_t>(lane) * kIwBoxes + nn] =
+                G[(sx + i) + 5 * ((sy + jj) + 5 * (sz + k))];
+          }
+        } else {
+          bits |= kStOverflow;
+        }
+        ++nn;
+      }
+      __syncwarp();
+    }
+    // the verdict rules of finalize_slot, level by level
+    if (bits & kStInvalid) return make_flag(kVInvalid, child_level, 0);
+    if (bits & (kStAmbig | kStOverflow)) return -1;
+    if (nn == 0) return (bits & kStCap) ? make_flag(kVUndecided, p.max_depth, 0)
+                                        : make_flag(kVValid, child_level, 0);
+    nb = nn;
+    cur ^= 1;
+  }
+  return -1;  // not reached: the last level queues nothing
+}
+
 // Warp-cooperative fp64_element (element64.cuh): element e of the batch,
 // all 32 lanes, `sm` = this warp's shared scratch.
 static __device__ __noinline__ void fp64_element_warp(const Batch& p, uint32_t e, double* sm) {
@@ -232,6 +376,18 @@ static __device__ __noinline__ void fp64_element_warp(const Batch& p, uint32_t e
   }
   const double lo = dunkey(kmin), hi = dunkey(kmax);
   if (outcome == 2) {
+    const int f = refine_in_warp(p, un, E, fmax(fabs(lo), fabs(hi)) + E, sm);
+    if (f >= 0) {
+      if (lane == 0) {
+        atomicAdd(&S.cnt->iw_done, 1u);
+        p.flags[g] = static_cast<uint8_t>(f);
+        if (p.bmin) p.bmin[g] = lo;
+        if (p.bmax) p.bmax[g] = hi;
+      }
+      return;
+    }
+  }
+  if (outcome == 2) {
     // tensor position of this lane's coefficient
     int t = -1;
     if (lane < 8) t = corner_t(lane);
@@ -270,17 +426,6 @@ static __device__ __noinline__ void fp64_element_warp(const Batch& p, uint32_t e
   }
   if (p.bmin) p.bmin[g] = lo;
   if (p.bmax) p.bmax[g] = hi;
-}
-
-__device__ __forceinline__ void split5_row(const double* in, int stride_in, double* out,
-                                           int stride_out) {
-  double p0 = in[0], p1 = in[stride_in], p2 = in[2 * stride_in];
-  double s = p0 + p1, t = p1 + p2;
-  out[0] = p0;
-  out[stride_out] = 0.5 * s;
-  out[2 * stride_out] = 0.25 * (s + t);
-  out[3 * stride_out] = 0.5 * t;
-  out[4 * stride_out] = p2;
 }
 
 // Warp-cooperative refine_box: box `idx` of level `level`, all 32 lanes.

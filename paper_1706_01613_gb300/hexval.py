@@ -348,14 +348,14 @@ class Validator:
         tensors) to the device, runs the check and copies the flags back.
         kind = "soa" (corners) or "indexed" (nodes, conn).  Returns the host
         flags tensor (uint8)."""
+        import torch
         dev = [a.to(self.device, non_blocking=True) for a in arrays]
+        n = dev[0].shape[2] if kind == "soa" else dev[1].shape[0]
+        flags = torch.empty(n, dtype=torch.uint8, device=self.device)
         if kind == "soa":
-            flags, _, _ = self.check_soa(dev[0], out=self._outputs(dev[0].shape[2], None)[:1]
-                                         + (None, None), stream=stream)
+            self.check_soa(dev[0], out=(flags, None, None), stream=stream)
         else:
-            flags, _, _ = self.check_indexed(dev[0], dev[1],
-                                             out=self._outputs(dev[1].shape[0], None)[:1]
-                                             + (None, None), stream=stream)
+            self.check_indexed(dev[0], dev[1], out=(flags, None, None), stream=stream)
         return flags.to("cpu")
 
     def status(self, stream=None):
