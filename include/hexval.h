@@ -80,23 +80,36 @@ typedef struct {
   uint32_t reserved[2];    /* must be 0 */
 } hexval_config;
 
-/* options (tuning knobs, same results):
+/* options (tuning knobs; the same flags, and with HEXVAL_OPT_DFREDO the
+ * bounds of the elements it decides carry its error instead of FP64's):
  *  HEXVAL_OPT_PAIR32   the FP32 bulk pass with two elements per thread in
  *                      packed f32x2 arithmetic instead of one per thread;
  *  HEXVAL_OPT_PREFETCH the indexed FP32 bulk pass on a persistent grid that
  *                      stages its inputs through shared memory with
  *                      asynchronous copies: connectivity two tiles ahead,
  *                      node records one tile ahead (ignored with
- *                      HEXVAL_OPT_PAIR32). */
-enum { HEXVAL_OPT_PAIR32 = 1, HEXVAL_OPT_PREFETCH = 2 };
+ *                      HEXVAL_OPT_PAIR32);
+ *  HEXVAL_OPT_DFREDO   FP32 form: the escalations the FP32 pass leaves are
+ *                      first redone in double-float (pairs of FP32 values,
+ *                      about 44 bits, at FP32 throughput) by a kernel of its
+ *                      own; those it decides at depth 0 are final (bmin/bmax
+ *                      within (2^-31 L + 2^-38 X) L^2 of the exact values, L
+ *                      the largest edge-vector component, X the largest
+ *                      |coordinate|), the rest go on to FP64.  Pays for one
+ *                      more launch per batch; worth it when many elements
+ *                      escalate (near-degenerate meshes). */
+enum { HEXVAL_OPT_PAIR32 = 1, HEXVAL_OPT_PREFETCH = 2, HEXVAL_OPT_DFREDO = 4 };
 
 typedef struct {
   uint64_t elements;        /* elements processed since the last reset */
-  uint64_t escalated_fp64;  /* FP32 decisions redone in FP64 */
+  uint64_t escalated_fp64;  /* FP32 decisions redone at higher precision
+                               (double-float or FP64) */
   uint64_t refined;         /* elements that needed subdivision */
   uint64_t boxes;           /* boxes examined by the refinement */
   uint64_t exact;           /* elements decided by the exact tier */
   uint64_t max_level_boxes; /* largest refinement level (boxes) */
+  uint64_t escalated_df;    /* of escalated_fp64: decided in double-float
+                               (pairs of FP32 values, about 44 bits) */
 } hexval_stats;
 
 /* Fills *cfg with the defaults listed above. */
@@ -235,6 +248,7 @@ enum {
   HEXVAL_PH_TAIL = 3,    /* FP64 redo of FP32 escalations, refinement and
                             the exact tier (one launch) */
   HEXVAL_PH_EXACT = 4,   /* unused: the exact tier runs inside the tail */
+  HEXVAL_PH_REDODF = 5,  /* double-float redo of escalations (HEXVAL_OPT_DFREDO) */
   HEXVAL_PH_COUNT = 8
 };
 typedef struct {

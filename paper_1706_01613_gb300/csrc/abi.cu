@@ -104,6 +104,8 @@ int run_batches(hexval_ctx* h, Batch p, int64_t n_hex, cudaStream_t st) {
     const bool fp32 = c.precision == HEXVAL_FP32_FILTERED;
     cudaError_t e = fp32 ? phase(h, HEXVAL_PH_BULK32, st, [&] { return hexval::launch_bulk32(p, st); })
                          : phase(h, HEXVAL_PH_BULK64, st, [&] { return hexval::launch_bulk64(p, st); });
+    if (e == cudaSuccess && fp32 && p.dfredo)
+      e = phase(h, HEXVAL_PH_REDODF, st, [&] { return hexval::launch_redo_df(p, st); });
     if (e == cudaSuccess)
       e = phase(h, HEXVAL_PH_TAIL, st, [&] { return hexval::launch_tail(p, fp32, st); });
     if (e != cudaSuccess) {
@@ -141,7 +143,7 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
   if (cfg->max_batch == 0 || cfg->max_batch > (1ull << 31) || cfg->queue_capacity == 0 ||
       cfg->queue_capacity > (1ull << 31) || cfg->exact_capacity == 0 ||
       cfg->exact_capacity > (1ull << 31) || cfg->max_nodes > (1ull << 31) ||
-      (cfg->options & ~static_cast<uint32_t>(HEXVAL_OPT_PAIR32 | HEXVAL_OPT_PREFETCH)) ||
+      (cfg->options & ~static_cast<uint32_t>(HEXVAL_OPT_PAIR32 | HEXVAL_OPT_PREFETCH | HEXVAL_OPT_DFREDO)) ||
       cfg->reserved[0] ||
       cfg->reserved[1] ||
       (cfg->bulk_threads != 0 && cfg->bulk_threads != 64 && cfg->bulk_threads != 128 &&
@@ -177,7 +179,8 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
          alloc(h, &s.s32_elem, cfg->max_batch) && alloc(h, &s.s32_state, cfg->max_batch) &&
          alloc(h, &s.s32_lev, cfg->max_batch) && alloc(h, &s.s32_e0, cfg->max_batch) &&
          alloc(h, &s.s32_m0, cfg->max_batch) &&
-         alloc(h, &s.iw, static_cast<uint64_t>(hexval::kIwSlots) * 2 * 27 * hexval::kIwBoxes);
+         alloc(h, &s.iw, static_cast<uint64_t>(hexval::kIwSlots) * 2 * 27 * hexval::kIwBoxes) &&
+         alloc(h, &s.esc3, cfg->max_batch);
   }
   if (!ok) {
     free_all(h);
@@ -221,6 +224,7 @@ int hexval_check_soa(hexval_handle h, int64_t n_hex, const double* corners, uint
   p.stride = n_hex;
   p.indexed = 0;
   p.pair32 = (h->cfg.options & HEXVAL_OPT_PAIR32) != 0;
+  p.dfredo = (h->cfg.options & HEXVAL_OPT_DFREDO) != 0;
   p.bulk_threads = static_cast<int>(h->cfg.bulk_threads);
   p.flags = flags;
   p.bmin = bmin;
@@ -249,6 +253,7 @@ int hexval_check_indexed(hexval_handle h, int64_t n_nodes, const double* nodes, 
   p.indexed = 1;
   p.pair32 = (h->cfg.options & HEXVAL_OPT_PAIR32) != 0;
   p.prefetch32 = (h->cfg.options & HEXVAL_OPT_PREFETCH) != 0;
+  p.dfredo = (h->cfg.options & HEXVAL_OPT_DFREDO) != 0;
   p.bulk_threads = static_cast<int>(h->cfg.bulk_threads);
   p.flags = flags;
   p.bmin = bmin;
@@ -427,6 +432,7 @@ int hexval_get_stats(hexval_handle h, hexval_stats* out, int reset, void* stream
   out->boxes = s.boxes;
   out->exact = s.exact;
   out->max_level_boxes = s.max_level_boxes;
+  out->escalated_df = s.escalated_df;
   if (reset && cudaMemset(h->s.stats, 0, sizeof(s)) != cudaSuccess) return HEXVAL_E_CUDA;
   return HEXVAL_OK;
 }

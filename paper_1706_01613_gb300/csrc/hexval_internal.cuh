@@ -58,7 +58,9 @@ struct Counters {
   unsigned int minj_next;                   // element counter of the minimum-of-J kernel
   unsigned int iw_count;                    // in-warp refinement workspaces taken
   unsigned int iw_done;                     // elements decided by the in-warp refinement
-  unsigned int pad[4];
+  unsigned int esc3_count;                  // double-float redo -> tail (list esc3)
+  unsigned int df_count;                    // decided by the double-float redo
+  unsigned int pad[2];
 };
 
 // Escalations of the FP32 pass: the first kEscInBulk elements appended to
@@ -81,7 +83,8 @@ constexpr unsigned int kIwBoxes = 64;
 
 // Counters accumulated across calls (hexval_get_stats).
 struct Stats {
-  unsigned long long elements, escalated_fp64, refined, boxes, exact, max_level_boxes;
+  unsigned long long elements, escalated_fp64, refined, boxes, exact, max_level_boxes,
+      escalated_df;
 };
 
 // Device scratch owned by a handle.
@@ -127,6 +130,8 @@ struct Scratch {
   float* s32_m0;
   // FP32 form: workspaces of the in-warp FP64 refinement (warp_items.cuh)
   double* iw;
+  // FP32 form: elements the double-float redo leaves to FP64 (redo_df.cu)
+  uint32_t* esc3;
 };
 
 // One batch of elements, as seen by every kernel.
@@ -143,6 +148,7 @@ struct Batch {
   int pair32;        // FP32 pass: two elements per thread with packed f32x2 math
   int bulk_threads;  // block size of the bulk kernels (0: default)
   int prefetch32;    // indexed FP32 pass on a persistent grid with prefetch
+  int dfredo;        // FP32 form: escalations redone in double-float first
   // outputs (indexed by base + e)
   uint8_t* flags;
   double* bmin;
@@ -574,6 +580,9 @@ cudaError_t launch_bulk64(const Batch& p, cudaStream_t st);
 cudaError_t launch_bulk32(const Batch& p, cudaStream_t st);
 cudaError_t launch_nodes32(const Batch& p, cudaStream_t st);
 cudaError_t launch_tail(const Batch& p, bool from_list, cudaStream_t st);
+// FP32 form with HEXVAL_OPT_DFREDO: double-float redo of the escalations
+// the FP32 pass leaves (between the bulk and tail kernels).
+cudaError_t launch_redo_df(const Batch& p, cudaStream_t st);
 cudaError_t launch_quads(const QuadBatch& p, bool fp32, cudaStream_t st);
 cudaError_t launch_quality(const Batch& p, float* sj, cudaStream_t st);
 cudaError_t launch_minj(const Batch& p, double rel_tol, int max_depth, double* lo, double* hi,

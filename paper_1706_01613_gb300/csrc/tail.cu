@@ -251,6 +251,7 @@ __device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned in
                               (nr - nr_here) + ldcg(&C->iw_done));
   atomicAdd(&st->boxes, boxes);
   atomicAdd(&st->exact, static_cast<unsigned long long>(nx));
+  atomicAdd(&st->escalated_df, static_cast<unsigned long long>(ldcg(&C->df_count)));
   atomicMax(&st->max_level_boxes, mx);
   unsigned int* w = reinterpret_cast<unsigned int*>(C);
   for (unsigned int k = 0; k < sizeof(Counters) / sizeof(unsigned int); ++k) w[k] = 0u;
@@ -260,9 +261,12 @@ __device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned in
 __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from_list) {
   const Scratch& S = p.s;
   Counters* C = S.cnt;
-  // escalation list entries [kEscInBulk, n_list) are left for this kernel
+  // escalation list entries [kEscInBulk, n_list) are left for this kernel,
+  // or, after the double-float redo, the esc3 list it leaves
   const unsigned int n_list = from_list ? ldcg(&C->esc_count) : 0u;
-  const unsigned int n_esc = n_list > kEscInBulk ? n_list - kEscInBulk : 0u;
+  const unsigned int n_esc = !from_list ? 0u
+                             : p.dfredo ? ldcg(&C->esc3_count)
+                                        : (n_list > kEscInBulk ? n_list - kEscInBulk : 0u);
   // refinement list entries [kR32InBulk, n_rl) are left for this kernel
   const unsigned int n_rl = from_list ? ldcg(&C->r32_count) : 0u;
   const unsigned int n_r = n_rl > kR32InBulk ? n_rl - kR32InBulk : 0u;
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
     n_esc2 = ldcg(&C->esc2_count);
   }
   if (n_esc + n_esc2) {  // phase E: list entries, then the FP32 refinement's
-    const uint32_t* esc = S.esc + kEscInBulk;
+    const uint32_t* esc = p.dfredo ? S.esc3 : S.esc + kEscInBulk;
     const unsigned int n_e = n_esc + n_esc2;
     if (n_e <= warp_items) {
       FOR_EACH_WARP_ITEM(n_e, i)

@@ -22,6 +22,7 @@ CODES = {0: "HEXVAL_OK", -1: "HEXVAL_E_ARG", -2: "HEXVAL_E_NOMEM", -3: "HEXVAL_E
 FP64, FP32_FILTERED = 0, 1
 OPT_PAIR32 = 1    # hexval_config.options: packed f32x2 FP32 bulk pass
 OPT_PREFETCH = 2  # hexval_config.options: persistent indexed FP32 pass with prefetch
+OPT_DFREDO = 4    # hexval_config.options: double-float redo of FP32 escalations
 VALID, INVALID, UNDECIDED, NONFINITE = 1, 2, 3, 4
 
 # every function declared in include/hexval.h (the CPU test checks the list)
@@ -31,7 +32,7 @@ EXPORTS = ("hexval_config_default", "hexval_create", "hexval_destroy", "hexval_c
            "hexval_check_quads_indexed", "hexval_corner_quality",
            "hexval_corner_quality_indexed", "hexval_compact", "hexval_min_jacobian",
            "hexval_min_jacobian_indexed", "hexval_strerror")
-PHASES = ("nodes32", "bulk32", "bulk64", "tail", "exact", "-", "-", "-")
+PHASES = ("nodes32", "bulk32", "bulk64", "tail", "-", "redo_df", "-", "-")
 
 
 class Config(ctypes.Structure):
@@ -45,7 +46,8 @@ class Config(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
-                ("elements", "escalated_fp64", "refined", "boxes", "exact", "max_level_boxes")]
+                ("elements", "escalated_fp64", "refined", "boxes", "exact", "max_level_boxes",
+                 "escalated_df")]
 
 
 class Profile(ctypes.Structure):
