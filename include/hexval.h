@@ -97,8 +97,16 @@ typedef struct {
  *                      the largest edge-vector component, X the largest
  *                      |coordinate|), the rest go on to FP64.  Pays for one
  *                      more launch per batch; worth it when many elements
- *                      escalate (near-degenerate meshes). */
-enum { HEXVAL_OPT_PAIR32 = 1, HEXVAL_OPT_PREFETCH = 2, HEXVAL_OPT_DFREDO = 4 };
+ *                      escalate (near-degenerate meshes);
+ *  HEXVAL_OPT_NO_REPLAY every check call launched directly.  By default a
+ *                      check call identical to the previous one on the
+ *                      handle (entry point, pointers, sizes), made with
+ *                      profiling off on a stream that is not capturing, is
+ *                      captured once into a CUDA graph (on a private
+ *                      stream) that further identical calls launch: one
+ *                      launch per call instead of three or more.  The
+ *                      capture itself costs one host-side graph build. */
+enum { HEXVAL_OPT_PAIR32 = 1, HEXVAL_OPT_PREFETCH = 2, HEXVAL_OPT_DFREDO = 4, HEXVAL_OPT_NO_REPLAY = 8 };
 
 typedef struct {
   uint64_t elements;        /* elements processed since the last reset */

@@ -23,6 +23,7 @@ FP64, FP32_FILTERED = 0, 1
 OPT_PAIR32 = 1    # hexval_config.options: packed f32x2 FP32 bulk pass
 OPT_PREFETCH = 2  # hexval_config.options: persistent indexed FP32 pass with prefetch
 OPT_DFREDO = 4    # hexval_config.options: double-float redo of FP32 escalations
+OPT_NO_REPLAY = 8 # hexval_config.options: no graph replay of repeated check calls
 VALID, INVALID, UNDECIDED, NONFINITE = 1, 2, 3, 4
 
 # every function declared in include/hexval.h (the CPU test checks the list)

@@ -268,6 +268,39 @@ def test_double_float_redo_of_many_escalations(kind):
     assert runs[1][1]["escalated_df"] == 0
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_repeated_calls_replay_a_graph(prec):
+    """Identical calls are replayed from a graph the library captures on the
+    second one: results equal the direct launches', in-place changes of the
+    inputs between calls are seen, and other pointers fall back to direct
+    launches (and then a new graph)."""
+    nodes, conn = synth.structured_grid(40, 30, 20, sigma=0.3, seed=91)
+    N, C = torch.from_numpy(nodes).cuda(), torch.from_numpy(conn).cuda()
+    n = len(conn)
+    direct = hv.Validator(precision=prec, max_depth=8, options=hv.OPT_NO_REPLAY, **CAPS)
+    v = hv.Validator(precision=prec, max_depth=8, **CAPS)
+    out = tuple(torch.empty(n, dtype=d, device="cuda") for d in (torch.uint8, torch.float64, torch.float64))
+    ref = [t.cpu().numpy() for t in direct.check_indexed(N, C)]
+    for _ in range(4):  # direct, capture + replay, replay, replay
+        got = [t.cpu().numpy() for t in v.check_indexed(N, C, out=out)]
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b, equal_nan=True)
+    N[conn[7, 6]] += torch.tensor([0.0, 0.0, -3.0], dtype=torch.float64, device="cuda")  # inverts element 7
+    ref2 = [t.cpu().numpy() for t in direct.check_indexed(N, C)]
+    got = [t.cpu().numpy() for t in v.check_indexed(N, C, out=out)]
+    assert got[0][7] & 7 == 2
+    for a, b in zip(got, ref2):
+        assert np.array_equal(a, b, equal_nan=True)
+    X = synth.perturbed_cubes(3001, noise=0.5, seed=92)
+    want = oracle.check_soa(X, max_depth=8)
+    Xd = torch.from_numpy(X).cuda()
+    for _ in range(3):
+        _compare(prec, [t.cpu().numpy() for t in v.check_soa(Xd)], want)
+    assert v.status() == 0 and direct.status() == 0
+    v.close()
+    direct.close()
+
+
 def test_cuda_graph_capture_replays():
     X = torch.from_numpy(synth.perturbed_cubes(5000, noise=0.5, seed=3)).cuda()
     v = hv.Validator(precision="fp32", max_depth=8, **CAPS)
