@@ -1,7 +1,7 @@
 """Benchmark of the GB300 linear-hexahedron validity test.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config 2|1|3|4]
+                    [--config 2|1|3|4|4b]
 
 A step is one pass of the whole hot path (bulk pass, refinement, exact tier)
 over one synthetic workload already resident in HBM.  The default workload
@@ -66,6 +66,13 @@ def workload(cfg, rank):
         return dict(kind="soa", X=X, n=X.shape[2], depth=10,
                     name="4,194,304 twisted boundary-layer hexes (SoA FP64, depth cap 10)",
                     bytes_per_hex=192 + 17, n_nodes=0)
+    if cfg == "4b":  # stress variant: twists up to 180 degrees, deep refinement
+        X = synth.twisted_layers(4_194_304, seed=20170004 + 1000 * rank, theta_max_deg=180.0)
+        return dict(kind="soa", X=X, n=X.shape[2], depth=10,
+                    name="4,194,304 boundary-layer hexes twisted by up to 180 degrees "
+                         "(SoA FP64, depth cap 10)",
+                    bytes_per_hex=192 + 17, n_nodes=0,
+                    caps=dict(queue_capacity=1 << 25))  # ~2.6 live boxes per element
     raise ValueError(cfg)
 
 
@@ -465,7 +472,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--config", type=lambda c: c if c == "4b" else int(c), default=2,
+                    choices=[1, 2, 3, 4, "4b"])
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -530,9 +538,9 @@ def main():
         tuned = {"options": args.options, "bulk_threads": args.bulk_threads}
     else:
         tuned = tune.best_config("fp32", w["kind"], w["n"], dev_in, retune=args.retune,
-                                 max_depth=w["depth"])
-    v32 = hv.Validator(precision="fp32", max_depth=w["depth"], **tuned)
-    v64 = hv.Validator(precision="fp64", max_depth=w["depth"])
+                                 max_depth=w["depth"], **w.get("caps", {}))
+    v32 = hv.Validator(precision="fp32", max_depth=w["depth"], **tuned, **w.get("caps", {}))
+    v64 = hv.Validator(precision="fp64", max_depth=w["depth"], **w.get("caps", {}))
 
     clocks = ClockSampler(bus)
     if rank == 0:

@@ -101,17 +101,21 @@ def best_config(precision, kind, n, dev_inputs, cache=CACHE, retune=False, reps=
     for cfg in candidates(precision):
         results.append((time_config(cfg, precision, kind, dev_inputs, reps=reps, **caps), cfg))
     results.sort(key=lambda r: r[0])
-    best_ms, best = results[0]
+    # the leaders are often within noise of each other: timed again, longer
+    final = sorted(((time_config(c, precision, kind, dev_inputs, reps=3 * reps, **caps), c)
+                    for _, c in results[:3]), key=lambda r: r[0])
+    best_ms, best = final[0]
     if precision == "fp32":
         # the double-float redo pays off only when many elements escalate,
         # which depends on the data: tried on the winner
         dfr = dict(best, options=best["options"] | hv.OPT_DFREDO)
-        ms = time_config(dfr, precision, kind, dev_inputs, reps=reps, **caps)
+        ms = time_config(dfr, precision, kind, dev_inputs, reps=3 * reps, **caps)
         results.append((ms, dfr))
         if ms < best_ms:
             best_ms, best = ms, dfr
     data[key] = {"config": best, "ms": best_ms,
-                 "all": [{"config": c, "ms": m} for m, c in results]}
+                 "all": [{"config": c, "ms": m} for m, c in results],
+                 "final": [{"config": c, "ms": m} for m, c in final]}
     if cache:
         _save_cache(cache, data)
     return dict(best)
