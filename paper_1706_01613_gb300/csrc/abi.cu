@@ -252,8 +252,12 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
   s.exact_cap = cfg->exact_capacity;
   s.max_nodes = cfg->max_nodes;
   s.exact_work_words = hexval::exact_work_words();
+  s.xb_cap = hexval::kXbCap;
   bool ok = alloc(h, &s.qcoef[0], 27 * s.qcap) && alloc(h, &s.qcoef[1], 27 * s.qcap) &&
             alloc(h, &s.qslot[0], s.qcap) && alloc(h, &s.qslot[1], s.qcap) &&
+            alloc(h, &s.qpos[0], s.qcap) && alloc(h, &s.qpos[1], s.qcap) &&
+            alloc(h, &s.xb_slot, s.xb_cap) && alloc(h, &s.xb_qi, s.xb_cap) &&
+            alloc(h, &s.xb_pos, s.xb_cap) &&
             alloc(h, &s.slot_elem, s.qcap) && alloc(h, &s.slot_state, s.qcap) &&
             alloc(h, &s.slot_lev, s.qcap) && alloc(h, &s.slot_e0, s.qcap) &&
             alloc(h, &s.slot_m0, s.qcap) && alloc(h, &s.esc, cfg->max_batch) &&

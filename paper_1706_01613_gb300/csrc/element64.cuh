@@ -126,6 +126,7 @@ __device__ __forceinline__ void push_root(const Batch& p, unsigned int slot, uin
   S.slot_e0[slot] = E;
   S.slot_m0[slot] = M;
   S.qslot[0][slot] = slot;
+  if (S.qpos[0]) S.qpos[0][slot] = 0ull;
   double t[27];
   store_tensor(s, t);
 #pragma unroll

@@ -175,9 +175,12 @@ __device__ __forceinline__ int q_weight(int L, int t) {
   return on ? 1 : 0;
 }
 
-// Flag byte (without the exact bit) of element e if it is decided at depth
-// 0, else -1.  All 32 lanes call it; `sm` holds kFastWords words.
-static __device__ __noinline__ int exact_depth0_warp(const Batch& p, uint32_t e, uint32_t* sm) {
+// The 20 samples of element e as exact integers (Sec. 5), by the whole warp:
+// coordinates scaled to integers (sm[0, 96): 24 x 4 words), sample t in
+// sm[96 + 12 t, +12) (lanes t < 20 compute them).  Returns false when the
+// coordinates span more than kFastBits bits (then nothing is written).  All
+// 32 lanes call it; `sm` holds kFastWords words.
+__device__ __forceinline__ bool fast_samples_warp(const Batch& p, uint32_t e, uint32_t* sm) {
   const int lane = threadIdx.x & 31;
   const int64_t g = p.base + e;
   // coordinate of this lane (lanes 0-23: node lane / 3, axis lane % 3)
@@ -205,7 +208,7 @@ static __device__ __noinline__ int exact_depth0_warp(const Batch& p, uint32_t e,
   }
   const int qmin = __reduce_min_sync(kFull, qlo), top = __reduce_max_sync(kFull, qhi);
   const int B = top >= qmin ? top - qmin + 1 : 0;
-  if (B > kFastBits) return -1;
+  if (B > kFastBits) return false;
   uint32_t* Xs = sm;        // 24 coordinates x 4 words
   uint32_t* Ss = sm + 96;   // 20 samples x 12 words
   if (lane < 24) {
@@ -224,7 +227,6 @@ static __device__ __noinline__ int exact_depth0_warp(const Batch& p, uint32_t e,
     for (int i = 0; i < 4; ++i) Xs[4 * lane + i] = x.v[i];
   }
   __syncwarp();
-  bool pos = true;
   if (lane < 20) {  // sample `lane`: det(A, B, C) = A . (B x C)
     int ia, ib, ic;
     sample_columns(lane, ia, ib, ic);
@@ -244,35 +246,140 @@ static __device__ __noinline__ int exact_depth0_warp(const Batch& p, uint32_t e,
       const Wide<8> cr = wsub(wmul(Bv[d1], C[d2]), wmul(Bv[d2], C[d1]));
       acc = wadd(acc, wmul(A[d], cr));
     }
-    pos = wpositive(acc);
 #pragma unroll
     for (int i = 0; i < 12; ++i) Ss[12 * lane + i] = acc.v[i];
   }
-  if (__any_sync(kFull, !pos)) return make_flag(kVInvalid, 0, 0);  // Step 2
   __syncwarp();
-  bool cpos = true;  // corners (lanes 0-7) are the positive samples
-  if (lane >= 8 && lane < 27) {
+  return true;
+}
+
+// Scaled Table t:Tsmall coefficient of class lane L (0-7 corners, 8-19 edges,
+// 20-25 faces, 26 centre; as in fp64_element_warp) from the samples in Ss,
+// modulo 2^384.
+__device__ __forceinline__ Wide<12> class_value(const uint32_t* Ss, int L) {
+  Wide<12> acc;
+  if (L < 8) {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc.v[i] = Ss[12 * L + i];
+    return acc;
+  }
+#pragma unroll
+  for (int i = 0; i < 12; ++i) acc.v[i] = 0u;
+  for (int t = 0; t < 20; ++t) {
+    const int wgt = q_weight(L, t);
+    if (wgt == 0) continue;
+    const unsigned int a = static_cast<unsigned int>(wgt < 0 ? -wgt : wgt);
+    Wide<12> term;
+    unsigned long long c = 0;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {  // a x sample t, modulo 2^384
+      c += static_cast<unsigned long long>(a) * Ss[12 * t + i];
+      term.v[i] = static_cast<uint32_t>(c);
+      c >>= 32;
+    }
+    acc = wgt < 0 ? wsub(acc, term) : wadd(acc, term);
+  }
+  return acc;
+}
+
+// Flag byte (without the exact bit) of element e if it is decided at depth
+// 0, else -1.  All 32 lanes call it; `sm` holds kFastWords words.
+static __device__ __noinline__ int exact_depth0_warp(const Batch& p, uint32_t e, uint32_t* sm) {
+  const int lane = threadIdx.x & 31;
+  if (!fast_samples_warp(p, e, sm)) return -1;
+  const uint32_t* Ss = sm + 96;
+  bool pos = true;
+  if (lane < 20) {
     Wide<12> acc;
 #pragma unroll
-    for (int i = 0; i < 12; ++i) acc.v[i] = 0u;
-    for (int t = 0; t < 20; ++t) {
-      const int wgt = q_weight(lane, t);
-      if (wgt == 0) continue;
-      const unsigned int a = static_cast<unsigned int>(wgt < 0 ? -wgt : wgt);
-      Wide<12> term;
-      unsigned long long c = 0;
-#pragma unroll
-      for (int i = 0; i < 12; ++i) {  // a x sample t, modulo 2^384
-        c += static_cast<unsigned long long>(a) * Ss[12 * t + i];
-        term.v[i] = static_cast<uint32_t>(c);
-        c >>= 32;
-      }
-      acc = wgt < 0 ? wsub(acc, term) : wadd(acc, term);
-    }
-    cpos = wpositive(acc);
+    for (int i = 0; i < 12; ++i) acc.v[i] = Ss[12 * lane + i];
+    pos = wpositive(acc);
   }
+  if (__any_sync(kFull, !pos)) return make_flag(kVInvalid, 0, 0);  // Step 2
+  bool cpos = true;  // corners (lanes 0-7) are the positive samples
+  if (lane >= 8 && lane < 27) cpos = wpositive(class_value(Ss, lane));
   if (__all_sync(kFull, cpos)) return make_flag(kVValid, 0, 0);  // Step 4
   return -1;
+}
+
+// Exact signs of the coefficients of one box of the refinement: the box of
+// depth `level` at dyadic position (x, y, z) = pos (16 bits each) of element
+// e.  The root coefficients b (Table t:Tsmall) as integers scaled by 8 (and
+// by the coordinate scaling, a positive power of 2) in 480-bit words; then,
+// along xi, eta and zeta in turn, the Bernstein coefficients of the quadratic
+// on [s/n, (s+1)/n] (n = 2^level) scaled by n^2, exactly what `level`
+// halvings by de Casteljau give, up to that positive factor:
+//   n^2 c0 = (n-s)^2 b0 + 2 s (n-s) b1 + s^2 b2
+//   n^2 c1 = (n-s)(n-s-1) b0 + ((n-s)(s+1) + s(n-s-1)) b1 + s(s+1) b2
+//   n^2 c2 = (n-s-1)^2 b0 + 2 (s+1)(n-s-1) b1 + (s+1)^2 b2.
+// Widths: |8 b| < 2^377, every pass multiplies the magnitude by at most n^2 <=
+// 2^30, so the values stay below 2^467 < 2^479.  Returns 0 (a corner
+// coefficient <= 0), 1 (all 27 > 0), 2 (corners > 0, another <= 0), or -1
+// when the coordinates are outside the fast tier's range.  All 32 lanes call
+// it; `sm` holds at least 27 x 15 and kFastWords words.
+constexpr int kBoxWords = 15;
+static __device__ __noinline__ int exact_box_warp(const Batch& p, uint32_t e, int level,
+                                                  uint64_t pos, uint32_t* sm) {
+  const int lane = threadIdx.x & 31;
+  if (!fast_samples_warp(p, e, sm)) return -1;
+  Wide<kBoxWords> c;
+  int t = 0;  // tensor position i + 3 j + 9 k of this lane's coefficient
+  if (lane < 27) {
+    const Wide<12> v = class_value(sm + 96, lane);
+    // unscaled x 8: corners c x 8, edges 2b x 4, faces 4b x 2, centre 8b
+    const int sh = lane < 8 ? 3 : (lane < 20 ? 2 : (lane < 26 ? 1 : 0));
+    c = wext<kBoxWords>(v);
+    for (int r = 0; r < sh; ++r) c = wadd(c, c);
+    t = lane < 8 ? corner_t(lane)
+                 : (lane < 20 ? edge_t(lane - 8) : (lane < 26 ? face_t(lane - 20) : tix(1, 1, 1)));
+  }
+  __syncwarp();
+  uint32_t* W = sm;  // [27][kBoxWords], over the samples (read above)
+  if (lane < 27)
+#pragma unroll
+    for (int i = 0; i < kBoxWords; ++i) W[kBoxWords * t + i] = c.v[i];
+  __syncwarp();
+  const unsigned int n = 1u << level;
+  const int ti = lane % 3, tj = (lane / 3) % 3, tk = lane / 9;  // lane = tensor position now
+  for (int axis = 0; axis < 3; ++axis) {
+    const unsigned int s = static_cast<unsigned int>((pos >> (16 * axis)) & 0xffffu);
+    const int r = axis == 0 ? ti : (axis == 1 ? tj : tk);  // output index along the axis
+    const unsigned int a = n - s, b = s + 1, am = n - s - 1;
+    unsigned int w[3];
+    if (r == 0) { w[0] = a * a; w[1] = 2u * s * a; w[2] = s * s; }
+    else if (r == 1) { w[0] = a * am; w[1] = a * b + s * am; w[2] = s * b; }
+    else { w[0] = am * am; w[1] = 2u * b * am; w[2] = b * b; }
+    Wide<kBoxWords> acc;
+#pragma unroll
+    for (int i = 0; i < kBoxWords; ++i) acc.v[i] = 0u;
+    if (lane < 27) {
+      const int stride = axis == 0 ? 1 : (axis == 1 ? 3 : 9);
+      const int base = lane - r * stride;
+      for (int m = 0; m < 3; ++m) {
+        const uint32_t* src = W + kBoxWords * (base + m * stride);
+        Wide<kBoxWords> term;
+        unsigned long long cy = 0;
+#pragma unroll
+        for (int i = 0; i < kBoxWords; ++i) {  // w[m] x coefficient, modulo 2^480
+          cy += static_cast<unsigned long long>(w[m]) * src[i];
+          term.v[i] = static_cast<uint32_t>(cy);
+          cy >>= 32;
+        }
+        acc = wadd(acc, term);
+      }
+    }
+    __syncwarp();
+    if (lane < 27)
+#pragma unroll
+      for (int i = 0; i < kBoxWords; ++i) W[kBoxWords * lane + i] = acc.v[i];
+    __syncwarp();
+    c = acc;
+  }
+  const bool corner = lane < 27 && ti != 1 && tj != 1 && tk != 1;
+  const bool positive = lane < 27 && wpositive(c);
+  if (__any_sync(kFull, corner && !positive)) return 0;
+  if (__all_sync(kFull, lane >= 27 || positive)) return 1;
+  return 2;
 }
 
 }  // namespace exact_tier

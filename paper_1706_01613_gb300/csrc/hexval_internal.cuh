@@ -33,6 +33,16 @@ constexpr uint32_t kStInvalid = 1u;   // a certified non-positive corner on the 
 constexpr uint32_t kStAmbig = 2u;     // an uncertifiable sign: exact tier needed
 constexpr uint32_t kStCap = 4u;       // uncertified box at the depth cap
 constexpr uint32_t kStOverflow = 8u;  // a child did not fit in the queue: exact tier
+constexpr uint32_t kStXUsed = 16u;    // a box sign was settled exactly (flag bit 7)
+
+// A refinement-queue entry whose slot id carries this bit is skipped (a box
+// the exact check certified after it was queued).
+constexpr uint32_t kDeadBox = 0x80000000u;
+// Exact-check list entry without a queued box (child on the last level).
+constexpr uint32_t kNoBox = 0xffffffffu;
+// Entries of the exact-check list of a batch (boxes whose signs FP64 cannot
+// settle, checked exactly one by one).
+constexpr uint64_t kXbCap = 1u << 16;
 
 // sticky device status bits
 constexpr uint32_t kSbIndex = 1u;
@@ -60,7 +70,8 @@ struct Counters {
   unsigned int iw_done;                     // elements decided by the in-warp refinement
   unsigned int esc3_count;                  // double-float redo -> tail (list esc3)
   unsigned int df_count;                    // decided by the double-float redo
-  unsigned int pad[2];
+  unsigned int xb_count;                    // exact-check list (boxes)
+  unsigned int pad[1];
 };
 
 // Escalations of the FP32 pass: the first kEscInBulk elements appended to
@@ -90,9 +101,18 @@ struct Stats {
 // Device scratch owned by a handle.
 struct Scratch {
   // refinement queue: two level buffers, SoA [27][cap] coefficients + slot ids
+  // + box positions (x | y << 16 | z << 32 on the dyadic grid of the level;
+  // optional: without them every uncertain sign goes to the full exact tier)
   double* qcoef[2];
   uint32_t* qslot[2];
+  uint64_t* qpos[2];
   uint64_t qcap;
+  // exact-check list: slot, queue position of the box in the next level (or
+  // kNoBox), box position; capacity xb_cap (0: no exact check)
+  uint32_t* xb_slot;
+  uint32_t* xb_qi;
+  uint64_t* xb_pos;
+  uint64_t xb_cap;
   // per refined element ("slot"), indexed by its position in level 0
   uint32_t* slot_elem;
   uint32_t* slot_state;

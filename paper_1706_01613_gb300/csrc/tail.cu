@@ -63,7 +63,12 @@ __device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool ac
   const int child_level = level + 1;
   const bool last = child_level >= p.max_depth;
   uint32_t slot = act ? ldcg(S.qslot[in] + idx) : 0u;
+  if (slot & kDeadBox) act = false;  // certified by the exact check
+  slot &= ~kDeadBox;
   if (act) act = !(ldcg(S.slot_state + slot) & (kStInvalid | kStAmbig | kStOverflow));
+  // exact check of uncertain children possible (box positions kept)
+  const bool xok = S.xb_cap != 0 && S.qpos[in] != nullptr;
+  const uint64_t ppos = (act && xok) ? ldcg(S.qpos[in] + idx) : 0ull;
   double G[5][5][5];
   uint32_t key = 0;
   if (act) {
@@ -101,6 +106,7 @@ __device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool ac
   }
   uint32_t bits = 0;   // element state bits found by this box
   uint32_t queue = 0;  // children to queue
+  uint32_t xq = 0;     // children whose class an uncertain sign decides: exact check
   if (act) {
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
@@ -121,20 +127,24 @@ __device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool ac
               amb2 |= !(q.nonpos | q.pos);
             }
           }
+      const bool unsure = !nonpos && (amb || (!notcert && amb2));
       if (nonpos) {
         bits |= kStInvalid;
-      } else if (amb) {
-        bits |= kStAmbig;
+      } else if (unsure) {
+        if (xok) {  // queued as if not certified; the exact check may drop it
+          xq |= 1u << o;
+          if (!last) queue |= 1u << o;
+        } else {
+          bits |= kStAmbig;
+        }
       } else if (notcert) {
         if (last)
           bits |= kStCap;
         else
           queue |= 1u << o;
-      } else if (amb2) {
-        bits |= kStAmbig;
       }
     }
-    if (bits & kStInvalid) queue = 0;  // the element is decided on this level
+    if (bits & kStInvalid) queue = xq = 0;  // the element is decided on this level
   }
   // one atomic per warp for all the children the warp queues
   const unsigned int lane = threadIdx.x & 31u;
@@ -151,8 +161,25 @@ __device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool ac
     if (lane == 31) pos = atomicAdd(&S.cnt->level_count[child_level], total);
     pos = __shfl_sync(0xffffffffu, pos, 31) + incl - cnt;
   }
+  unsigned int xpos = 0;
+  if (__any_sync(0xffffffffu, xq != 0u)) {  // rare
+    const unsigned int xc = __popc(xq);
+    unsigned int xincl = xc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      unsigned int v = __shfl_up_sync(0xffffffffu, xincl, d);
+      if (lane >= static_cast<unsigned int>(d)) xincl += v;
+    }
+    const unsigned int xtotal = __shfl_sync(0xffffffffu, xincl, 31);
+    if (lane == 31) xpos = atomicAdd(&S.cnt->xb_count, xtotal);
+    xpos = __shfl_sync(0xffffffffu, xpos, 31) + xincl - xc;
+  }
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
+    const uint64_t cpos = 2ull * ppos + (static_cast<uint64_t>(o & 1) |
+                                         (static_cast<uint64_t>((o >> 1) & 1) << 16) |
+                                         (static_cast<uint64_t>(o >> 2) << 32));
+    uint32_t qi = kNoBox;
     if ((queue >> o) & 1u) {
       if (pos < S.qcap) {
         const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
@@ -165,10 +192,22 @@ __device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool ac
             for (int i = 0; i < 3; ++i)
               dst[static_cast<uint64_t>(tix(i, j, k)) * S.qcap + pos] = G[sx + i][sy + j][sz + k];
         S.qslot[out][pos] = slot;
+        if (xok) S.qpos[out][pos] = cpos;
+        qi = pos;
       } else {
         bits |= kStOverflow;
       }
       ++pos;
+    }
+    if ((xq >> o) & 1u) {
+      if (xpos < S.xb_cap) {
+        S.xb_slot[xpos] = slot;
+        S.xb_qi[xpos] = qi;
+        S.xb_pos[xpos] = cpos;
+      } else {
+        bits |= kStAmbig;  // list full: the full exact tier decides the element
+      }
+      ++xpos;
     }
   }
   if (act) {
@@ -190,8 +229,9 @@ __device__ HEXVAL_TAIL_INLINE void finalize_slot(const Batch& p, bool act, unsig
   unsigned int pos = warp_append(&S.cnt->exact_count, to_exact);
   if (!act) return;
   uint8_t flag;
+  const int xu = (st & kStXUsed) ? 1 : 0;  // a box sign settled exactly
   if (st & kStInvalid) {
-    flag = make_flag(kVInvalid, lev, 0);
+    flag = make_flag(kVInvalid, lev, xu);
   } else if (to_exact) {
     if (pos < S.exact_cap) {
       S.exact_list[pos] = e;
@@ -200,11 +240,40 @@ __device__ HEXVAL_TAIL_INLINE void finalize_slot(const Batch& p, bool act, unsig
     set_status(S.status, kSbQueue);
     flag = make_flag(kVUndecided, p.max_depth, 0);
   } else if (st & kStCap) {
-    flag = make_flag(kVUndecided, p.max_depth, 0);
+    flag = make_flag(kVUndecided, p.max_depth, xu);
   } else {
-    flag = make_flag(kVValid, lev, 0);
+    flag = make_flag(kVValid, lev, xu);
   }
   p.flags[p.base + e] = flag;
+}
+
+// Exact check of entry i of the exact-check list (a child of depth `level`
+// whose class an uncertain sign decides; exact_warp.cuh): a corner <= 0
+// makes the element INVALID on this level; all 27 > 0 certify the box, whose
+// queue entry is then marked dead; otherwise the box stays queued, or hits
+// the cap on the last level.  Coordinates outside the fast exact range send
+// the element to the full exact tier.  All 32 lanes call it.
+__device__ __forceinline__ void exact_check_box(const Batch& p, int level, unsigned int i,
+                                                double* sm) {
+  const Scratch& S = p.s;
+  const uint32_t slot = ldcg(S.xb_slot + i);
+  if (ldcg(S.slot_state + slot) & (kStInvalid | kStAmbig | kStOverflow)) return;
+  const uint32_t qi = ldcg(S.xb_qi + i);
+  const int r = exact_tier::exact_box_warp(p, ldcg(S.slot_elem + slot), level,
+                                           ldcg(S.xb_pos + i), reinterpret_cast<uint32_t*>(sm));
+  if ((threadIdx.x & 31) == 0) {
+    if (r < 0) {
+      atomicOr(&S.slot_state[slot], kStAmbig);
+      atomicAdd(&S.cnt->amb_count, 1u);
+    } else {
+      uint32_t bits = kStXUsed;
+      if (r == 0) bits |= kStInvalid;
+      if (r == 2 && qi == kNoBox) bits |= kStCap;
+      atomicOr(&S.slot_state[slot], bits);
+      if (r == 1 && qi != kNoBox) S.qslot[level & 1][qi] = slot | kDeadBox;
+    }
+  }
+  __syncwarp();
 }
 
 // Work items of a grid-wide step are dealt to warps round robin over the
@@ -278,6 +347,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
   }
   __shared__ double wsm[kTailThreads / 32][kWarpScratch];
   static_assert(exact_tier::kFastWords <= 2 * kWarpScratch, "warp scratch too small");
+  static_assert(27 * exact_tier::kBoxWords <= 2 * kWarpScratch, "warp scratch too small");
   double* mysm = wsm[threadIdx.x >> 5];
   const unsigned int warp_items = kWarpItemsMax * gridDim.x * (blockDim.x >> 5);
   unsigned int epoch = 0;
@@ -309,6 +379,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
     grid_barrier(&C->arrive, epoch, S.status);
   }
   const unsigned int n0 = min(ldcg(&C->level_count[0]), static_cast<unsigned int>(S.qcap));
+  unsigned int xb_done = 0;  // exact-check entries settled so far
   for (int level = 0; n0 && level < p.max_depth; ++level) {
     const unsigned int n = min(ldcg(&C->level_count[level]),
                                static_cast<unsigned int>(S.qcap));
@@ -319,6 +390,13 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
       FOR_EACH_ITEM(n, i, act) refine_box(p, level, act, i);
     }
     grid_barrier(&C->arrive, epoch, S.status);
+    // exact check of the children of this level that an uncertain sign left open
+    const unsigned int nxb = min(ldcg(&C->xb_count), static_cast<unsigned int>(S.xb_cap));
+    if (nxb > xb_done) {
+      FOR_EACH_WARP_ITEM(nxb - xb_done, i) exact_check_box(p, level + 1, xb_done + i, mysm);
+      xb_done = nxb;
+      grid_barrier(&C->arrive, epoch, S.status);
+    }
   }
   // Elements for the exact tier: those already listed, and those whose boxes
   // met an uncertain sign or a full queue (listed by phase F below).

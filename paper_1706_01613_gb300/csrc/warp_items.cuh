@@ -406,6 +406,7 @@ static __device__ __noinline__ void fp64_element_warp(const Batch& p, uint32_t e
         S.slot_e0[slot] = E;
         S.slot_m0[slot] = fmax(fabs(lo), fabs(hi)) + E;
         S.qslot[0][slot] = slot;
+        if (S.qpos[0]) S.qpos[0][slot] = 0ull;
       }
     } else {
       outcome = 3;  // queue full: exact tier
@@ -436,8 +437,12 @@ static __device__ __noinline__ void refine_box_warp(const Batch& p, int level, u
   const int in = level & 1, out = in ^ 1;
   const int child_level = level + 1;
   const bool last = child_level >= p.max_depth;
-  const uint32_t slot = ldcg(S.qslot[in] + idx);
+  const uint32_t sraw = ldcg(S.qslot[in] + idx);
+  if (sraw & kDeadBox) return;  // certified by the exact check
+  const uint32_t slot = sraw;
   if (ldcg(S.slot_state + slot) & (kStInvalid | kStAmbig | kStOverflow)) return;
+  const bool xok = S.xb_cap != 0 && S.qpos[in] != nullptr;
+  const uint64_t ppos = xok ? ldcg(S.qpos[in] + idx) : 0ull;
   double* A = sm;          // [i + 3 j + 9 k]
   double* P1 = sm + 27;    // [i + 5 (j + 3 k)], i < 5
   double* P2 = sm + 72;    // [i + 5 (j + 5 k)], i, j < 5
@@ -464,7 +469,7 @@ static __device__ __noinline__ void refine_box_warp(const Batch& p, int level, u
   __syncwarp();
   // lane o < 8 classifies child o
   uint32_t bits = 0;
-  bool want = false;
+  bool want = false, xwant = false;
   if (lane < 8) {
     const int sx = 2 * (lane & 1), sy = 2 * ((lane >> 1) & 1), sz = 2 * (lane >> 2);
     bool nonpos = false, amb = false, notcert = false, amb2 = false;
@@ -480,34 +485,64 @@ static __device__ __noinline__ void refine_box_warp(const Batch& p, int level, u
             amb2 |= !(q.nonpos | q.pos);
           }
         }
+    const bool unsure = !nonpos && (amb || (!notcert && amb2));
     if (nonpos) bits = kStInvalid;
-    else if (amb) bits = kStAmbig;
+    else if (unsure) {
+      if (xok) { xwant = true; want = !last; }  // exact check (refine_box in tail.cu)
+      else bits = kStAmbig;
+    }
     else if (notcert) { if (last) bits = kStCap; else want = true; }
-    else if (amb2) bits = kStAmbig;
   }
   bits = __reduce_or_sync(kFull, bits);
   uint32_t queue = __ballot_sync(kFull, want) & 0xffu;
-  if (bits & kStInvalid) queue = 0;
-  unsigned int base = 0;
+  uint32_t xq = __ballot_sync(kFull, xwant) & 0xffu;
+  if (bits & kStInvalid) queue = xq = 0;
+  unsigned int base = 0, xbase = 0;
   if (queue) {
     if (lane == 0) base = atomicAdd(&S.cnt->level_count[child_level], __popc(queue));
     base = __shfl_sync(kFull, base, 0);
   }
-  unsigned int pos = base;
-  for (uint32_t q = queue; q; q &= q - 1) {
+  if (xq) {
+    if (lane == 0) xbase = atomicAdd(&S.cnt->xb_count, __popc(xq));
+    xbase = __shfl_sync(kFull, xbase, 0);
+  }
+  unsigned int pos = base, xpos = xbase;
+  for (uint32_t q = queue | xq; q; q &= q - 1) {
     const int o = __ffs(q) - 1;
-    if (pos < S.qcap) {
-      const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
-      if (lane < 27) {
-        int i = lane % 3, j = (lane / 3) % 3, k = lane / 9;
-        S.qcoef[out][static_cast<uint64_t>(lane) * S.qcap + pos] =
-            G[(sx + i) + 5 * ((sy + j) + 5 * (sz + k))];
+    const uint64_t cpos = 2ull * ppos + (static_cast<uint64_t>(o & 1) |
+                                         (static_cast<uint64_t>((o >> 1) & 1) << 16) |
+                                         (static_cast<uint64_t>(o >> 2) << 32));
+    uint32_t qi = kNoBox;
+    if ((queue >> o) & 1u) {
+      if (pos < S.qcap) {
+        const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
+        if (lane < 27) {
+          int i = lane % 3, j = (lane / 3) % 3, k = lane / 9;
+          S.qcoef[out][static_cast<uint64_t>(lane) * S.qcap + pos] =
+              G[(sx + i) + 5 * ((sy + j) + 5 * (sz + k))];
+        }
+        if (lane == 0) {
+          S.qslot[out][pos] = slot;
+          if (xok) S.qpos[out][pos] = cpos;
+        }
+        qi = pos;
+      } else {
+        bits |= kStOverflow;
       }
-      if (lane == 0) S.qslot[out][pos] = slot;
-    } else {
-      bits |= kStOverflow;
+      ++pos;
     }
-    ++pos;
+    if ((xq >> o) & 1u) {
+      if (xpos < S.xb_cap) {
+        if (lane == 0) {
+          S.xb_slot[xpos] = slot;
+          S.xb_qi[xpos] = qi;
+          S.xb_pos[xpos] = cpos;
+        }
+      } else {
+        bits |= kStAmbig;  // list full: the full exact tier decides the element
+      }
+      ++xpos;
+    }
   }
   if (lane == 0) {
     if (bits) atomicOr(&S.slot_state[slot], bits);

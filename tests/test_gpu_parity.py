@@ -301,6 +301,40 @@ def test_repeated_calls_replay_a_graph(prec):
     direct.close()
 
 
+def test_exact_box_checks_settle_deep_uncertain_boxes():
+    """65,536 prisms twisted by up to 180 degrees (depth cap 10), where some
+    boxes deep in the refinement have coefficients within the FP64 error
+    bound of zero.  Each such box is checked exactly on its own (the root
+    coefficients as integers, subdivided to the box by the exact Bernstein
+    formulas) instead of sending its element through the full exact tier.
+    Flags equal the oracle's on every element that used an exact box check
+    and on a sample of the others, in both forms, and a call takes seconds."""
+    import time
+    X = synth.twisted_layers(65536, seed=20170004, theta_max_deg=180.0)
+    got = {}
+    for prec in ("fp64", "fp32"):
+        v = hv.Validator(precision=prec, max_depth=10)
+        Xd = torch.from_numpy(X).cuda()
+        v.check_soa(Xd)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        f = v.check_soa(Xd)[0].cpu().numpy()
+        dt = time.time() - t0
+        assert v.status() == 0
+        v.close()
+        assert dt < 5.0, dt
+        got[prec] = f
+    used = np.union1d(np.nonzero(got["fp64"] & 0x80)[0], np.nonzero(got["fp32"] & 0x80)[0])
+    print("elements with an exact box check:", len(used))
+    assert len(used) > 0
+    rest = np.random.default_rng(6).choice(X.shape[2], 3000, replace=False)
+    idx = np.union1d(used, rest)
+    wf, _, _ = oracle.check_soa(np.ascontiguousarray(X[:, :, idx]), max_depth=10)
+    for prec in ("fp64", "fp32"):
+        bad = np.nonzero((got[prec][idx] & 0x7F) != (wf & 0x7F))[0]
+        assert len(bad) == 0, (prec, idx[bad[:10]], got[prec][idx[bad[:10]]], wf[bad[:10]])
+
+
 def test_cuda_graph_capture_replays():
     X = torch.from_numpy(synth.perturbed_cubes(5000, noise=0.5, seed=3)).cuda()
     v = hv.Validator(precision="fp32", max_depth=8, **CAPS)
