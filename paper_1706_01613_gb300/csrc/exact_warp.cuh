@@ -283,10 +283,12 @@ __device__ __forceinline__ Wide<12> class_value(const uint32_t* Ss, int L) {
 }
 
 // Flag byte (without the exact bit) of element e if it is decided at depth
-// 0, else -1.  All 32 lanes call it; `sm` holds kFastWords words.
+// 0; -1 when it needs refinement (every sample > 0, a coefficient <= 0); -2
+// when its coordinates are outside the fast range.  All 32 lanes call it;
+// `sm` holds kFastWords words.
 static __device__ __noinline__ int exact_depth0_warp(const Batch& p, uint32_t e, uint32_t* sm) {
   const int lane = threadIdx.x & 31;
-  if (!fast_samples_warp(p, e, sm)) return -1;
+  if (!fast_samples_warp(p, e, sm)) return -2;
   const uint32_t* Ss = sm + 96;
   bool pos = true;
   if (lane < 20) {

@@ -3,9 +3,12 @@
 //           the escalation list are redone in FP64 (element64.cuh);
 //  levels   refinement of undecided elements (Sec. 6, recursive_subdivision),
 //           breadth first, one level per grid-wide step;
+//  phase X0 elements whose root signs could not be certified: decided
+//           exactly at depth 0, or refined from their FP64 root box;
 //  phase F  verdicts of the refined elements;
-//  phase X  the exact tier (exact.cuh) for elements whose signs could not be
-//           certified, only when some element needs it.
+//  phase X  the full exact tier (exact.cuh) for what is left (coordinates
+//           outside the fast exact range, a full queue or list), only when
+//           some element needs it.
 // Grid-wide steps are separated by a bounded grid barrier.  Every count that
 // decides a branch is read after a barrier (or was written by an earlier
 // launch), so all blocks take the same branches; with nothing to do the
@@ -22,7 +25,8 @@
 //   all 27 certainly > 0                         -> child certified
 //   corners certainly > 0, another certainly <=0 -> child queued for d+2
 //                                                   (or the cap is hit)
-//   a sign that the error bound cannot settle    -> element goes exact.
+//   a sign that the error bound cannot settle    -> exact check of the box
+//                                                   after the level.
 // INVALID found on a level wins over anything else found on that level, which
 // gives the order-independent verdict (shallowest level with a non-positive
 // corner) whatever the order in which boxes are processed.
@@ -276,6 +280,64 @@ __device__ __forceinline__ void exact_check_box(const Batch& p, int level, unsig
   __syncwarp();
 }
 
+// Element of exact-list entry i whose root an uncertain sign left open
+// (listed by the depth-0 passes), before the refinement levels: decided
+// exactly at depth 0 when it can be; when it needs subdivision (every sample
+// > 0, a coefficient <= 0, both exactly) its FP64 root box enters level 0 of
+// the refinement like any other, with the exact box check for later
+// uncertain signs.  Entries handled here are replaced by kNoBox; the others
+// (coordinates outside the fast exact range, a full queue) stay for the full
+// tier.  All 32 lanes call it.
+__device__ __forceinline__ void exact_root_entry(const Batch& p, unsigned int i, double* sm) {
+  const Scratch& S = p.s;
+  const int lane = threadIdx.x & 31;
+  const uint32_t e = ldcg(S.exact_list + i);
+  const int64_t g = p.base + e;
+  const int f = exact_tier::exact_depth0_warp(p, e, reinterpret_cast<uint32_t*>(sm));
+  if (f == -2) return;
+  if (f >= 0 || p.max_depth == 0) {
+    if (lane == 0) {
+      p.flags[g] = f >= 0 ? static_cast<uint8_t>(f | 0x80) : make_flag(kVUndecided, 0, 1);
+      S.exact_list[i] = kNoBox;
+    }
+    __syncwarp();
+    return;
+  }
+  double smp, coef, E;
+  if (warp_root64(p, g, sm, smp, coef, E)) return;
+  const double un =
+      lane < 8 ? coef : (lane < 20 ? coef * 0.5 : (lane < 26 ? coef * 0.25 : coef * 0.125));
+  long long kmin = lane < 27 ? dkey(un) : 0x7fffffffffffffffLL;
+  long long kmax = lane < 27 ? dkey(un) : (-0x7fffffffffffffffLL - 1);
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    kmin = min(kmin, __shfl_xor_sync(kFull, kmin, d));
+    kmax = max(kmax, __shfl_xor_sync(kFull, kmax, d));
+  }
+  const double M0 = fmax(fabs(dunkey(kmin)), fabs(dunkey(kmax))) + E;
+  unsigned int slot = 0;
+  if (lane == 0) slot = atomicAdd(&S.cnt->level_count[0], 1u);
+  slot = __shfl_sync(kFull, slot, 0);
+  if (slot >= S.qcap) return;  // queue full: the full tier decides it
+  int t = -1;
+  if (lane < 8) t = corner_t(lane);
+  else if (lane < 20) t = edge_t(lane - 8);
+  else if (lane < 26) t = face_t(lane - 20);
+  else if (lane == 26) t = tix(1, 1, 1);
+  if (t >= 0) S.qcoef[0][static_cast<uint64_t>(t) * S.qcap + slot] = un;
+  if (lane == 0) {
+    S.slot_elem[slot] = e;
+    S.slot_state[slot] = kStXUsed;
+    S.slot_lev[slot] = 0u;
+    S.slot_e0[slot] = E;
+    S.slot_m0[slot] = M0;
+    S.qslot[0][slot] = slot;
+    S.qpos[0][slot] = 0ull;
+    S.exact_list[i] = kNoBox;
+  }
+  __syncwarp();
+}
+
 // Work items of a grid-wide step are dealt to warps round robin over the
 // blocks first, so that a short list is spread over all SMs (each warp takes
 // 32 consecutive items; the trip count is uniform within a warp).
@@ -378,6 +440,12 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
     }
     grid_barrier(&C->arrive, epoch, S.status);
   }
+  // phase X0: elements listed for the exact tier by the depth-0 passes
+  const unsigned int nx0 = min(ldcg(&C->exact_count), static_cast<unsigned int>(S.exact_cap));
+  if (nx0 && S.xb_cap && S.qpos[0]) {
+    FOR_EACH_WARP_ITEM(nx0, i) exact_root_entry(p, i, mysm);
+    grid_barrier(&C->arrive, epoch, S.status);
+  }
   const unsigned int n0 = min(ldcg(&C->level_count[0]), static_cast<unsigned int>(S.qcap));
   unsigned int xb_done = 0;  // exact-check entries settled so far
   for (int level = 0; n0 && level < p.max_depth; ++level) {
@@ -416,6 +484,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
          w += nwarps)
       for (unsigned int i = w; i < nx; i += exact_tier::kWorkers) {
         const uint32_t e = ldcg(S.exact_list + i);
+        if (e == kNoBox) continue;  // settled in phase X0
         const int flag = exact_tier::exact_depth0_warp(p, e, esm);
         if ((threadIdx.x & 31u) == 0u) {
           if (flag >= 0)
