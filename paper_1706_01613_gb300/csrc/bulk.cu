@@ -98,6 +98,8 @@ inline size_t scratch_bytes(int threads) {
 }
 
 __global__ void __launch_bounds__(kBulkThreads) bulk64_kernel(Batch p) {
+  pdl_wait();
+  pdl_trigger();
   unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool act = i < static_cast<unsigned int>(p.n);
   fp64_element(p, act, act ? i : 0u);
@@ -106,6 +108,8 @@ __global__ void __launch_bounds__(kBulkThreads) bulk64_kernel(Batch p) {
 // Decides what FP32 can decide; everything else is escalated to FP64.
 template <bool INDEXED>
 __global__ void __launch_bounds__(kBulkThreads, 4) bulk32_kernel(Batch p) {
+  pdl_wait();
+  pdl_trigger();
   const Scratch& S = p.s;
   unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool act = i < static_cast<unsigned int>(p.n);
@@ -179,6 +183,8 @@ inline size_t staged_bytes(int threads) {
 }
 
 __global__ void __launch_bounds__(kBulkThreads, 4) bulk32s_kernel(Batch p) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ float4 stage[];
   const Scratch& S = p.s;
   const unsigned int T = blockDim.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
@@ -289,6 +295,8 @@ constexpr int kPairThreads = 128;
 
 template <bool INDEXED>
 __global__ void __launch_bounds__(kPairThreads, 4) bulk32x2_kernel(Batch p) {
+  pdl_wait();
+  pdl_trigger();
   const Scratch& S = p.s;
   const unsigned int t = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned int i0 = 2 * t, i1 = 2 * t + 1;
@@ -384,6 +392,7 @@ __global__ void __launch_bounds__(kPairThreads, 4) bulk32x2_kernel(Batch p) {
 // touching such a node are escalated).
 __global__ void __launch_bounds__(256) nodes32_kernel(const double* nodes, int64_t n_nodes,
                                                       float4* out) {
+  pdl_trigger();
   int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n_nodes) return;
   bool bad = false;
@@ -396,6 +405,7 @@ __global__ void __launch_bounds__(256) nodes32_kernel(const double* nodes, int64
 // Two nodes per thread with 16-byte loads (nodes 16-byte aligned).
 __global__ void __launch_bounds__(256) nodes32x2_kernel(const double2* nodes, int64_t n_nodes,
                                                         float4* out) {
+  pdl_trigger();
   int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   int64_t i = 2 * t;
   if (i >= n_nodes) return;
@@ -420,8 +430,7 @@ cudaError_t launch_bulk64(const Batch& p, cudaStream_t st) {
   if (p.n <= 0) return cudaSuccess;
   const int bt = p.bulk_threads ? p.bulk_threads : kBulkThreads;
   unsigned int blocks = static_cast<unsigned int>((p.n + bt - 1) / bt);
-  bulk64_kernel<<<blocks, bt, 0, st>>>(p);
-  return cudaGetLastError();
+  return launch_pdl(bulk64_kernel, blocks, bt, 0, st, p);
 }
 
 cudaError_t launch_bulk32(const Batch& p, cudaStream_t st) {
@@ -431,25 +440,19 @@ cudaError_t launch_bulk32(const Batch& p, cudaStream_t st) {
     int64_t threads = (p.n + 1) / 2;
     unsigned int blocks = static_cast<unsigned int>((threads + bt - 1) / bt);
     if (p.indexed)
-      bulk32x2_kernel<true><<<blocks, bt, scratch_bytes(bt), st>>>(p);
-    else
-      bulk32x2_kernel<false><<<blocks, bt, scratch_bytes(bt), st>>>(p);
-    return cudaGetLastError();
+      return launch_pdl(bulk32x2_kernel<true>, blocks, bt, scratch_bytes(bt), st, p);
+    return launch_pdl(bulk32x2_kernel<false>, blocks, bt, scratch_bytes(bt), st, p);
   }
   const int bt = p.bulk_threads ? p.bulk_threads : kBulk32Default;
   if (p.indexed && p.prefetch32) {
     int64_t need = (p.n + bt - 1) / bt;
     int64_t blocks = bulk32s_blocks(bt);
-    bulk32s_kernel<<<static_cast<unsigned int>(need < blocks ? need : blocks), bt,
-                     staged_bytes(bt), st>>>(p);
-    return cudaGetLastError();
+    return launch_pdl(bulk32s_kernel, static_cast<unsigned int>(need < blocks ? need : blocks), bt,
+                      staged_bytes(bt), st, p);
   }
   unsigned int blocks = static_cast<unsigned int>((p.n + bt - 1) / bt);
-  if (p.indexed)
-    bulk32_kernel<true><<<blocks, bt, scratch_bytes(bt), st>>>(p);
-  else
-    bulk32_kernel<false><<<blocks, bt, scratch_bytes(bt), st>>>(p);
-  return cudaGetLastError();
+  if (p.indexed) return launch_pdl(bulk32_kernel<true>, blocks, bt, scratch_bytes(bt), st, p);
+  return launch_pdl(bulk32_kernel<false>, blocks, bt, scratch_bytes(bt), st, p);
 }
 
 cudaError_t launch_nodes32(const Batch& p, cudaStream_t st) {

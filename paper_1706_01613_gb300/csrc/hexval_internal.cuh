@@ -600,6 +600,32 @@ cudaError_t launch_bulk64(const Batch& p, cudaStream_t st);
 cudaError_t launch_bulk32(const Batch& p, cudaStream_t st);
 cudaError_t launch_nodes32(const Batch& p, cudaStream_t st);
 cudaError_t launch_tail(const Batch& p, bool from_list, cudaStream_t st);
+
+// Programmatic dependent launch: a kernel launched with launch_pdl may begin
+// (its blocks become resident) while the kernel before it in the stream
+// finishes; it calls pdl_wait before touching anything, which returns once
+// that kernel has completed and its writes are visible.  pdl_trigger lets
+// the next kernel begin launching.  Both are no-ops in a normal launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned int grid, unsigned int block,
+                              size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 // FP32 form with HEXVAL_OPT_DFREDO: double-float redo of the escalations
 // the FP32 pass leaves (between the bulk and tail kernels).
 cudaError_t launch_redo_df(const Batch& p, cudaStream_t st);

@@ -41,6 +41,8 @@ __device__ __forceinline__ void df_item(const Batch& p, bool act, uint32_t e) {
 }
 
 __global__ void __launch_bounds__(kRedoThreads, 4) redo_df_kernel(Batch p) {
+  pdl_wait();
+  pdl_trigger();
   const Scratch& S = p.s;
   const unsigned int n_list = ldcg(&S.cnt->esc_count);
   const unsigned int n = n_list > kEscInBulk ? n_list - kEscInBulk : 0u;
@@ -69,8 +71,7 @@ int redo_blocks() {
 }  // namespace
 
 cudaError_t launch_redo_df(const Batch& p, cudaStream_t st) {
-  redo_df_kernel<<<redo_blocks(), kRedoThreads, 0, st>>>(p);
-  return cudaGetLastError();
+  return launch_pdl(redo_df_kernel, static_cast<unsigned int>(redo_blocks()), kRedoThreads, 0, st, p);
 }
 
 }  // namespace hexval

@@ -359,37 +359,50 @@ constexpr unsigned int kWarpItemsMax = 8;
   for (unsigned int i = blockIdx.x + gridDim.x * (threadIdx.x >> 5); i < (n);      \
        i += gridDim.x * (blockDim.x >> 5))
 
-// Folds the batch counters into the statistics and resets them (one thread,
-// once every block of the batch's last kernel is done with the counters).
+// Folds the batch counters into the statistics and resets them: all threads
+// of one block, once every block of the batch's last kernel is done with the
+// counters.  Warp 0 reads them (the per-level counts one per lane), then the
+// block zeroes them together.
 __device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned int nx) {
   const Scratch& S = p.s;
   Counters* C = S.cnt;
-  __threadfence();
   Stats* st = S.stats;
-  unsigned long long boxes = 0, mx = 0;
-  for (int l = 1; l <= kMaxDepth + 1; ++l) {
-    const unsigned long long c = ldcg(&C->level_count[l]), c32 = ldcg(&C->level32_count[l]);
-    boxes += c + c32;
-    mx = c > mx ? c : mx;
-    mx = c32 > mx ? c32 : mx;
+  const unsigned int t = threadIdx.x;
+  if (t < 32) {
+    unsigned long long c = 0, c32 = 0;
+    if (t >= 1 && t <= kMaxDepth + 1) {
+      c = ldcg(&C->level_count[t]);
+      c32 = ldcg(&C->level32_count[t]);
+    }
+    unsigned long long boxes = c + c32, mx = c > c32 ? c : c32;
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+      boxes += __shfl_xor_sync(0xffffffffu, boxes, d);
+      const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, d);
+      mx = o > mx ? o : mx;
+    }
+    if (t == 0) {
+      const unsigned int nr = ldcg(&C->r32_count);
+      const unsigned int nr_here = nr < kR32InBulk ? nr : kR32InBulk;
+      atomicAdd(&st->elements, static_cast<unsigned long long>(p.n));
+      atomicAdd(&st->escalated_fp64, static_cast<unsigned long long>(ldcg(&C->esc_count)) +
+                                         ldcg(&C->esc2_count) + nr_here);
+      atomicAdd(&st->refined, static_cast<unsigned long long>(ldcg(&C->level_count[0])) +
+                                  (nr - nr_here) + ldcg(&C->iw_done));
+      atomicAdd(&st->boxes, boxes);
+      atomicAdd(&st->exact, static_cast<unsigned long long>(nx));
+      atomicAdd(&st->escalated_df, static_cast<unsigned long long>(ldcg(&C->df_count)));
+      atomicMax(&st->max_level_boxes, mx);
+    }
   }
-  atomicAdd(&st->elements, static_cast<unsigned long long>(p.n));
-  const unsigned int nr = ldcg(&C->r32_count);
-  const unsigned int nr_here = nr < kR32InBulk ? nr : kR32InBulk;
-  atomicAdd(&st->escalated_fp64, static_cast<unsigned long long>(ldcg(&C->esc_count)) +
-                                     ldcg(&C->esc2_count) + nr_here);
-  atomicAdd(&st->refined, static_cast<unsigned long long>(ldcg(&C->level_count[0])) +
-                              (nr - nr_here) + ldcg(&C->iw_done));
-  atomicAdd(&st->boxes, boxes);
-  atomicAdd(&st->exact, static_cast<unsigned long long>(nx));
-  atomicAdd(&st->escalated_df, static_cast<unsigned long long>(ldcg(&C->df_count)));
-  atomicMax(&st->max_level_boxes, mx);
+  __syncthreads();  // every read above is done before the reset
   unsigned int* w = reinterpret_cast<unsigned int*>(C);
-  for (unsigned int k = 0; k < sizeof(Counters) / sizeof(unsigned int); ++k) w[k] = 0u;
+  for (unsigned int k = t; k < sizeof(Counters) / sizeof(unsigned int); k += blockDim.x) w[k] = 0u;
   __threadfence();
 }
 
 __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from_list) {
+  pdl_wait();
   const Scratch& S = p.s;
   Counters* C = S.cnt;
   // escalation list entries [kEscInBulk, n_list) are left for this kernel,
@@ -404,7 +417,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
   if (n_esc == 0 && n_r == 0 && ldcg(&C->level_count[0]) == 0 && ldcg(&C->exact_count) == 0) {
     // nothing left: every block reads only counters that are, or become,
     // zero here, so block 0 may end the batch at once
-    if (blockIdx.x == 0 && threadIdx.x == 0) fold_stats_and_reset(p, 0u);
+    if (blockIdx.x == 0) fold_stats_and_reset(p, 0u);
     return;
   }
   __shared__ double wsm[kTailThreads / 32][kWarpScratch];
@@ -496,10 +509,16 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
       }
   }
   // the last block ends the batch
+  __shared__ int last_block;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    if (atomicAdd(&C->done, 1u) == gridDim.x - 1) fold_stats_and_reset(p, nx);
+    last_block = atomicAdd(&C->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last_block) {
+    __threadfence();
+    fold_stats_and_reset(p, nx);
   }
 }
 
@@ -521,9 +540,29 @@ uint64_t exact_work_words() {
   return static_cast<uint64_t>(exact_tier::kInts) * exact_tier::kLimbsMax * exact_tier::kWorkers;
 }
 
+// Cooperative (all blocks resident: the grid barrier) and, where the driver
+// accepts it, programmatic (it may become resident while the bulk pass
+// finishes; tail_kernel starts with pdl_wait).
 cudaError_t launch_tail(const Batch& p, bool from_list, cudaStream_t st) {
   Batch arg = p;
   int fl = from_list ? 1 : 0;
+  static int pdl_ok = 1;
+  if (pdl_ok) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(tail_blocks());
+    cfg.blockDim = dim3(kTailThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    if (cudaLaunchKernelEx(&cfg, tail_kernel, arg, fl) == cudaSuccess) return cudaSuccess;
+    cudaGetLastError();
+    pdl_ok = 0;  // not accepted: plain cooperative launches from now on
+  }
   void* args[] = {&arg, &fl};
   return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(tail_kernel), dim3(tail_blocks()),
                                      dim3(kTailThreads), args, 0, st);
