@@ -67,3 +67,37 @@ def test_binding_refuses_without_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         hv.Validator()
+
+
+def _header():
+    text = open(os.path.join(ROOT, "include", "hexval.h")).read()
+    return re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+
+
+def _enum_values(text):
+    return {k: int(v, 0) for k, v in re.findall(r"\b(HEXVAL_\w+)\s*=\s*(-?\w+)", text)}
+
+
+def test_binding_constants_match_the_header():
+    """Option bits, profile phases and the statistics record of the binding
+    are the header's."""
+    vals = _enum_values(_header())
+    assert vals["HEXVAL_OPT_PAIR32"] == hv.OPT_PAIR32
+    assert vals["HEXVAL_OPT_PREFETCH"] == hv.OPT_PREFETCH
+    assert vals["HEXVAL_OPT_DFREDO"] == hv.OPT_DFREDO
+    assert vals["HEXVAL_OPT_NO_REPLAY"] == hv.OPT_NO_REPLAY
+    assert len(hv.PHASES) == vals["HEXVAL_PH_COUNT"]
+    for name, ph in (("nodes32", "NODES32"), ("bulk32", "BULK32"), ("bulk64", "BULK64"),
+                     ("tail", "TAIL"), ("redo_df", "REDODF")):
+        assert hv.PHASES.index(name) == vals["HEXVAL_PH_" + ph]
+    body = re.search(r"typedef struct \{([^}]*)\} hexval_stats;", _header()).group(1)
+    fields = re.findall(r"uint64_t\s+(\w+);", body)
+    assert [f for f, _ in hv.Stats._fields_] == fields
+    for code, name in hv.CODES.items():
+        assert vals[name] == code
+
+
+def test_options_outside_the_known_bits_are_refused(lib):
+    bad = hv.default_config()
+    bad.options = 16
+    assert lib.hexval_create(ctypes.byref(bad), ctypes.byref(ctypes.c_void_p())) == -1
