@@ -57,7 +57,8 @@ enum {
 enum { HEXVAL_FP64 = 0, HEXVAL_FP32_FILTERED = 1 };
 
 /* verdict in bits 0-2 of a flag byte; bits 3-6 hold the decision depth,
- * bit 7 marks an element that needed the exact tier (diagnostic only) */
+ * bit 7 marks an element that needed exact arithmetic: the exact tier, or an
+ * exact check of one refinement box (diagnostic only) */
 enum {
   HEXVAL_VALID = 1,     /* J > 0 on the whole element */
   HEXVAL_INVALID = 2,   /* J <= 0 somewhere */
