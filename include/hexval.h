@@ -13,7 +13,8 @@
  *
  * Exactness: every sign decision is certified with a forward-error bound; a
  * decision the bound cannot settle is redone in higher precision (FP32 ->
- * FP64) and finally in exact integer arithmetic on the device, so the
+ * FP64) and finally in exact integer arithmetic on the device (the element
+ * at depth 0, or the one refinement box whose sign is uncertain), so the
  * verdicts are those of exact arithmetic on the FP64 inputs.
  *
  * Conventions shared by every entry point:
@@ -21,8 +22,10 @@
  *    says _host); the library never frees them and never keeps them after
  *    the call has been enqueued;
  *  - calls are stream ordered and enqueue only: no host synchronisation and
- *    no allocation (all scratch is owned by the handle, allocated in
- *    hexval_create); results are visible once the stream reaches them;
+ *    no device allocation (all scratch is owned by the handle, allocated in
+ *    hexval_create); results are visible once the stream reaches them.  The
+ *    one object a call may create is the replay graph of the check calls
+ *    (see HEXVAL_OPT_NO_REPLAY), on the second identical call;
  *  - one handle must not be used by two streams at the same time (its
  *    scratch is shared by the calls made on it);
  *  - host-detectable errors return a negative code and enqueue nothing;
