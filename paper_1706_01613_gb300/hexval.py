@@ -139,7 +139,9 @@ class Validator:
     precision: "fp64" (plain FP64 bulk pass) or "fp32" (FP32-filtered bulk
     pass with certified escalation).  The remaining keywords override fields
     of the default configuration (max_depth, queue_capacity, max_batch,
-    max_nodes, exact_capacity)."""
+    max_nodes, exact_capacity, bulk_threads, options = OPT_* bits: PAIR32,
+    PREFETCH, DFREDO, NO_REPLAY).  Repeated identical check calls are
+    replayed from a CUDA graph unless NO_REPLAY is set."""
 
     def __init__(self, precision="fp64", max_depth=8, device=None, **caps):
         import torch
