@@ -21,6 +21,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hexval_internal.cuh"
 
 using hexval::Batch;
@@ -101,9 +103,28 @@ void prof_drain(Profiler& P, int keep) {
   }
 }
 
+// NVTX range (host side: the enqueue of a phase or call) for timeline tools;
+// a no-op without an attached tool.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
+const char* phase_name(int ph) {
+  switch (ph) {
+    case HEXVAL_PH_NODES32: return "hexval nodes32";
+    case HEXVAL_PH_BULK32: return "hexval bulk32";
+    case HEXVAL_PH_BULK64: return "hexval bulk64";
+    case HEXVAL_PH_TAIL: return "hexval tail";
+    case HEXVAL_PH_REDODF: return "hexval redo_df";
+    default: return "hexval";
+  }
+}
+
 // Launches one phase, bracketed by timing events when profiling is on.
 template <typename F>
 cudaError_t phase(hexval_ctx* h, int ph, cudaStream_t st, F&& launch) {
+  NvtxRange range(phase_name(ph));
   Profiler& P = h->prof;
   if (!P.on) return launch();
   if (P.pending == Profiler::kPairs) prof_drain(P, Profiler::kPairs - 1);
@@ -186,6 +207,7 @@ bool capture_call(hexval_ctx* h, const Batch& p, int kind, int64_t n_hex) {
 
 // Direct launches, or the replay of a repeated call.
 int run_call(hexval_ctx* h, const Batch& p, int kind, int64_t n_hex, cudaStream_t st) {
+  NvtxRange range(kind ? "hexval_check_indexed" : "hexval_check_soa");
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if ((h->cfg.options & HEXVAL_OPT_NO_REPLAY) || h->prof.on ||
       cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
