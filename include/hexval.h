@@ -81,7 +81,11 @@ typedef struct {
   uint32_t options;        /* HEXVAL_OPT_* bits (default 0) */
   uint32_t bulk_threads;   /* threads per block of the bulk kernels: 0 (default: 256
                               for FP64, 128 for FP32), 64, 128 or 256 */
-  uint32_t reserved[2];    /* must be 0 */
+  uint32_t spin_limit;     /* polls of the tail kernel's grid barrier before it
+                              gives up with HEXVAL_E_TIMEOUT (0: the default,
+                              2^24, well over a second); a small value is for
+                              testing the timeout path */
+  uint32_t reserved;       /* must be 0 */
 } hexval_config;
 
 /* options (tuning knobs; the same flags, and with HEXVAL_OPT_DFREDO the
@@ -244,7 +248,11 @@ int hexval_min_jacobian_indexed(hexval_handle h, int64_t n_nodes, const double* 
                                 uint8_t* depth, void* stream);
 
 /* Synchronises the stream, returns the sticky device status (HEXVAL_OK or
- * the most severe device-detected code) and clears it. */
+ * the most severe device-detected code) and clears it.  After
+ * HEXVAL_E_TIMEOUT the batch that timed out is incomplete: its blocks stopped
+ * their work at the barrier (elements not yet decided keep whatever their
+ * flags held), while the batch counters were still folded and reset, so the
+ * handle stays usable. */
 int hexval_status(hexval_handle h, void* stream);
 
 /* Synchronises the stream and copies the counters; reset != 0 zeroes them. */

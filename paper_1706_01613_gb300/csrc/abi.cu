@@ -28,6 +28,11 @@
 using hexval::Batch;
 using hexval::Scratch;
 
+namespace hexval {
+// tail.cu: the tail launch with a grid-barrier budget (polls; <= 0: default)
+cudaError_t launch_tail(const Batch& p, bool from_list, long long spin_limit, cudaStream_t st);
+}  // namespace hexval
+
 // Event pairs for the optional per-phase timing.
 struct Profiler {
   static constexpr int kPairs = 2048;
@@ -54,6 +59,7 @@ struct Replay {
 
 struct hexval_ctx {
   hexval_config cfg;
+  long long spin_limit = 0;  // grid-barrier budget of the tail (0: default)
   Scratch s;
   void* blocks[48];
   int nblocks;
@@ -150,7 +156,8 @@ int run_batches(hexval_ctx* h, Batch p, int64_t n_hex, cudaStream_t st) {
     if (e == cudaSuccess && fp32 && p.dfredo)
       e = phase(h, HEXVAL_PH_REDODF, st, [&] { return hexval::launch_redo_df(p, st); });
     if (e == cudaSuccess)
-      e = phase(h, HEXVAL_PH_TAIL, st, [&] { return hexval::launch_tail(p, fp32, st); });
+      e = phase(h, HEXVAL_PH_TAIL, st,
+                [&] { return hexval::launch_tail(p, fp32, h->spin_limit, st); });
     if (e != cudaSuccess) {
       // the tail resets the counters; if it could not run, reset them here
       cudaGetLastError();
@@ -257,8 +264,7 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
       cfg->exact_capacity > (1ull << 31) || cfg->max_nodes > (1ull << 31) ||
       (cfg->options & ~static_cast<uint32_t>(HEXVAL_OPT_PAIR32 | HEXVAL_OPT_PREFETCH | HEXVAL_OPT_DFREDO |
                                              HEXVAL_OPT_NO_REPLAY)) ||
-      cfg->reserved[0] ||
-      cfg->reserved[1] ||
+      cfg->reserved ||
       (cfg->bulk_threads != 0 && cfg->bulk_threads != 64 && cfg->bulk_threads != 128 &&
        cfg->bulk_threads != 256))
     return HEXVAL_E_ARG;
@@ -275,6 +281,7 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
   s.max_nodes = cfg->max_nodes;
   s.exact_work_words = hexval::exact_work_words();
   s.xb_cap = hexval::kXbCap;
+  h->spin_limit = cfg->spin_limit;
   bool ok = alloc(h, &s.qcoef[0], 27 * s.qcap) && alloc(h, &s.qcoef[1], 27 * s.qcap) &&
             alloc(h, &s.qslot[0], s.qcap) && alloc(h, &s.qslot[1], s.qcap) &&
             alloc(h, &s.qpos[0], s.qcap) && alloc(h, &s.qpos[1], s.qcap) &&

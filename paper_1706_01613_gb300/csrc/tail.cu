@@ -359,6 +359,38 @@ constexpr unsigned int kWarpItemsMax = 8;
   for (unsigned int i = blockIdx.x + gridDim.x * (threadIdx.x >> 5); i < (n);      \
        i += gridDim.x * (blockDim.x >> 5))
 
+// Grid-wide barrier of the tail kernel (a cooperative launch: all blocks
+// co-resident) with a bounded wait: after `limit` polls of the arrival
+// counter (each an L2 round trip) the block records kSbTimeout and the
+// barrier returns false, after which the block does no further work of the
+// batch and only takes part in the end-of-kernel counter fold, so that no
+// block ever reads data another block may not have written.  Blocks waiting
+// at a later barrier then give up the same way.
+__device__ __forceinline__ bool tail_barrier(unsigned int* arrive, unsigned int& epoch,
+                                             uint32_t* status, long long limit) {
+  __shared__ int timed_out;
+  __syncthreads();
+  ++epoch;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(arrive, 1u);
+    const unsigned int target = epoch * gridDim.x;
+    long long spins = 0;
+    int to = 0;
+    while (ld_acquire(arrive) < target) {
+      if (++spins > limit) {
+        atomicOr(status, kSbTimeout);
+        to = 1;
+        break;
+      }
+    }
+    timed_out = to;
+    __threadfence();
+  }
+  __syncthreads();
+  return timed_out == 0;
+}
+
 // Folds the batch counters into the statistics and resets them: all threads
 // of one block, once every block of the batch's last kernel is done with the
 // counters.  Warp 0 reads them (the per-level counts one per lane), then the
@@ -401,7 +433,8 @@ __device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned in
   __threadfence();
 }
 
-__global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from_list) {
+__global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from_list,
+                                                             long long spin_limit) {
   pdl_wait();
   const Scratch& S = p.s;
   Counters* C = S.cnt;
@@ -427,21 +460,29 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
   const unsigned int warp_items = kWarpItemsMax * gridDim.x * (blockDim.x >> 5);
   unsigned int epoch = 0;
   unsigned int n_esc2 = 0;
+  // false once a grid barrier timed out: the block then skips to the end
+  bool go = true;
+  auto sync = [&]() {
+    go = go && tail_barrier(&C->arrive, epoch, S.status, spin_limit);
+    return go;
+  };
   if (n_r) {  // phase R: refinement in FP32 of the elements listed by the FP32 pass
     FOR_EACH_ITEM(n_r, i, act) root32(p, act, i);
-    grid_barrier(&C->arrive, epoch, S.status);
-    for (int level = 0; level < p.max_depth; ++level) {
+    sync();
+    for (int level = 0; go && level < p.max_depth; ++level) {
       const unsigned int n = min(level == 0 ? n_r : ldcg(&C->level32_count[level]),
                                  static_cast<unsigned int>(S.q32cap));
       if (n == 0) break;
       FOR_EACH_ITEM(n, i, act) refine_box32(p, level, act, i);
-      grid_barrier(&C->arrive, epoch, S.status);
+      sync();
     }
-    FOR_EACH_ITEM(n_r, i, act) finalize32(p, act, i);
-    grid_barrier(&C->arrive, epoch, S.status);
-    n_esc2 = ldcg(&C->esc2_count);
+    if (go) {
+      FOR_EACH_ITEM(n_r, i, act) finalize32(p, act, i);
+      sync();
+    }
+    if (go) n_esc2 = ldcg(&C->esc2_count);
   }
-  if (n_esc + n_esc2) {  // phase E: list entries, then the FP32 refinement's
+  if (go && n_esc + n_esc2) {  // phase E: list entries, then the FP32 refinement's
     const uint32_t* esc = p.dfredo ? S.esc3 : S.esc + kEscInBulk;
     const unsigned int n_e = n_esc + n_esc2;
     if (n_e <= warp_items) {
@@ -451,17 +492,18 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
       FOR_EACH_ITEM(n_e, i, act)
         fp64_item(p, act, act ? (i < n_esc ? ldcg(esc + i) : ldcg(S.esc2 + (i - n_esc))) : 0u);
     }
-    grid_barrier(&C->arrive, epoch, S.status);
+    sync();
   }
   // phase X0: elements listed for the exact tier by the depth-0 passes
   const unsigned int nx0 = min(ldcg(&C->exact_count), static_cast<unsigned int>(S.exact_cap));
-  if (nx0 && S.xb_cap && S.qpos[0]) {
+  if (go && nx0 && S.xb_cap && S.qpos[0]) {
     FOR_EACH_WARP_ITEM(nx0, i) exact_root_entry(p, i, mysm);
-    grid_barrier(&C->arrive, epoch, S.status);
+    sync();
   }
-  const unsigned int n0 = min(ldcg(&C->level_count[0]), static_cast<unsigned int>(S.qcap));
+  const unsigned int n0 =
+      go ? min(ldcg(&C->level_count[0]), static_cast<unsigned int>(S.qcap)) : 0u;
   unsigned int xb_done = 0;  // exact-check entries settled so far
-  for (int level = 0; n0 && level < p.max_depth; ++level) {
+  for (int level = 0; go && n0 && level < p.max_depth; ++level) {
     const unsigned int n = min(ldcg(&C->level_count[level]),
                                static_cast<unsigned int>(S.qcap));
     if (n == 0) break;
@@ -470,24 +512,24 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
     } else {
       FOR_EACH_ITEM(n, i, act) refine_box(p, level, act, i);
     }
-    grid_barrier(&C->arrive, epoch, S.status);
+    if (!sync()) break;
     // exact check of the children of this level that an uncertain sign left open
     const unsigned int nxb = min(ldcg(&C->xb_count), static_cast<unsigned int>(S.xb_cap));
     if (nxb > xb_done) {
       FOR_EACH_WARP_ITEM(nxb - xb_done, i) exact_check_box(p, level + 1, xb_done + i, mysm);
       xb_done = nxb;
-      grid_barrier(&C->arrive, epoch, S.status);
+      sync();
     }
   }
   // Elements for the exact tier: those already listed, and those whose boxes
   // met an uncertain sign or a full queue (listed by phase F below).
-  const bool exact = ldcg(&C->exact_count) != 0u || ldcg(&C->amb_count) != 0u;
-  if (n0) {  // phase F
+  const bool exact = go && (ldcg(&C->exact_count) != 0u || ldcg(&C->amb_count) != 0u);
+  if (go && n0) {  // phase F
     FOR_EACH_ITEM(n0, i, act) finalize_slot(p, act, i);
-    if (exact) grid_barrier(&C->arrive, epoch, S.status);
+    if (exact) sync();
   }
   unsigned int nx = 0;
-  if (exact) {
+  if (go && exact) {
     // phase X: the first kWorkers warps, one element at a time each; depth-0
     // decisions by the whole warp, anything deeper by lane 0 (full tier)
     nx = min(ldcg(&C->exact_count), static_cast<unsigned int>(S.exact_cap));
@@ -542,10 +584,12 @@ uint64_t exact_work_words() {
 
 // Cooperative (all blocks resident: the grid barrier) and, where the driver
 // accepts it, programmatic (it may become resident while the bulk pass
-// finishes; tail_kernel starts with pdl_wait).
-cudaError_t launch_tail(const Batch& p, bool from_list, cudaStream_t st) {
+// finishes; tail_kernel starts with pdl_wait).  spin_limit = polls of the
+// grid barrier before it gives up (kSpinLimit by default).
+cudaError_t launch_tail(const Batch& p, bool from_list, long long spin_limit, cudaStream_t st) {
   Batch arg = p;
   int fl = from_list ? 1 : 0;
+  long long lim = spin_limit > 0 ? spin_limit : kSpinLimit;
   static int pdl_ok = 1;
   if (pdl_ok) {
     cudaLaunchConfig_t cfg = {};
@@ -559,13 +603,17 @@ cudaError_t launch_tail(const Batch& p, bool from_list, cudaStream_t st) {
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    if (cudaLaunchKernelEx(&cfg, tail_kernel, arg, fl) == cudaSuccess) return cudaSuccess;
+    if (cudaLaunchKernelEx(&cfg, tail_kernel, arg, fl, lim) == cudaSuccess) return cudaSuccess;
     cudaGetLastError();
     pdl_ok = 0;  // not accepted: plain cooperative launches from now on
   }
-  void* args[] = {&arg, &fl};
+  void* args[] = {&arg, &fl, &lim};
   return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(tail_kernel), dim3(tail_blocks()),
                                      dim3(kTailThreads), args, 0, st);
+}
+
+cudaError_t launch_tail(const Batch& p, bool from_list, cudaStream_t st) {
+  return launch_tail(p, from_list, kSpinLimit, st);
 }
 
 }  // namespace hexval

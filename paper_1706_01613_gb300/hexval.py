@@ -42,7 +42,7 @@ class Config(ctypes.Structure):
                 ("max_batch", ctypes.c_uint64), ("queue_capacity", ctypes.c_uint64),
                 ("max_nodes", ctypes.c_uint64), ("exact_capacity", ctypes.c_uint64),
                 ("options", ctypes.c_uint32), ("bulk_threads", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 2)]
+                ("spin_limit", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):

@@ -101,3 +101,7 @@ def test_options_outside_the_known_bits_are_refused(lib):
     bad = hv.default_config()
     bad.options = 16
     assert lib.hexval_create(ctypes.byref(bad), ctypes.byref(ctypes.c_void_p())) == -1
+    bad = hv.default_config()
+    bad.reserved = 1
+    assert lib.hexval_create(ctypes.byref(bad), ctypes.byref(ctypes.c_void_p())) == -1
+    assert hv.default_config().spin_limit == 0  # the default budget

@@ -335,6 +335,26 @@ def test_exact_box_checks_settle_deep_uncertain_boxes():
         assert len(bad) == 0, (prec, idx[bad[:10]], got[prec][idx[bad[:10]]], wf[bad[:10]])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_barrier_wait_budget_runs_out_cleanly(prec):
+    """Failure detection without a fault: with a grid-barrier budget of one
+    poll the tail kernel's barriers give up, the status reads
+    HEXVAL_E_TIMEOUT, and the blocks stop their work and end the kernel; the
+    counters are still folded and reset, so the context and the handle stay
+    usable, and a handle with the default budget then gives the oracle's
+    flags on the same input."""
+    X = synth.twisted_layers(20_000, seed=4444, theta_max_deg=180.0)  # deep refinement
+    v = hv.Validator(precision=prec, max_depth=8, spin_limit=1, **CAPS)
+    rcs = [_run_soa(v, X)[3] for _ in range(5)]
+    v.close()
+    assert set(rcs) <= {0, -6} and -6 in rcs, rcs
+    w = hv.Validator(precision=prec, max_depth=8, **CAPS)
+    got = _run_soa(w, X)
+    assert got[3] == 0
+    _compare(prec, got[:3], oracle.check_soa(X, max_depth=8))
+    w.close()
+
+
 def test_cuda_graph_capture_replays():
     X = torch.from_numpy(synth.perturbed_cubes(5000, noise=0.5, seed=3)).cuda()
     v = hv.Validator(precision="fp32", max_depth=8, **CAPS)
