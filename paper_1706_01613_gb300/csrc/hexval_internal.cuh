@@ -505,31 +505,9 @@ __device__ __forceinline__ T ldcg(const T* p) {
   return __ldcg(p);
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident), with
-// a bounded wait: after kSpinLimit polls (each an L2 round trip, well over a
-// second in all) the block records kSbTimeout and goes on (results of that
-// call are then reported as unreliable by the status, and the kernel still
-// terminates).
+// Default budget (polls of the arrival counter, each an L2 round trip: well
+// over a second in all) of the tail kernel's bounded grid barrier (tail.cu).
 constexpr long long kSpinLimit = 1ll << 24;
-__device__ __forceinline__ void grid_barrier(unsigned int* arrive, unsigned int& epoch,
-                                             uint32_t* status) {
-  __syncthreads();
-  ++epoch;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(arrive, 1u);
-    const unsigned int target = epoch * gridDim.x;
-    long long spins = 0;
-    while (ld_acquire(arrive) < target) {
-      if (++spins > kSpinLimit) {
-        atomicOr(status, kSbTimeout);
-        break;
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-}
 
 // ---------------------------------------------------- element loading ------
 // Loads the 8 nodes (24 coordinates) of element g of the batch.  Returns
