@@ -28,47 +28,10 @@
 #pragma once
 
 #include "element32.cuh"
+// after the FP64 code above: its fma calls must not see the double-float fma
+#include "df_arith.cuh"
 
 namespace hexval {
-
-struct DF {
-  float hi, lo;
-  DF() = default;
-  __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
-  __device__ __forceinline__ explicit DF(int v) : hi(static_cast<float>(v)), lo(0.f) {}
-};
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  e = b - (s - a);
-}
-__device__ __forceinline__ DF operator+(const DF& x, const DF& y) {
-  float s, t, u, v;
-  two_sum(x.hi, y.hi, s, t);
-  two_sum(x.lo, y.lo, u, v);
-  t += u;
-  fast_two_sum(s, t, s, t);
-  t += v;
-  fast_two_sum(s, t, s, t);
-  return DF(s, t);
-}
-__device__ __forceinline__ DF operator-(const DF& x) { return DF(-x.hi, -x.lo); }
-__device__ __forceinline__ DF operator-(const DF& x, const DF& y) { return x + (-y); }
-__device__ __forceinline__ DF operator*(const DF& x, const DF& y) {
-  const float p = x.hi * y.hi;
-  float e = fmaf(x.hi, y.hi, -p);
-  e = fmaf(x.hi, y.lo, e);
-  e = fmaf(x.lo, y.hi, e);
-  float s, t;
-  fast_two_sum(p, e, s, t);
-  return DF(s, t);
-}
-__device__ __forceinline__ DF fma(const DF& a, const DF& b, const DF& c) { return a * b + c; }
 
 __device__ __forceinline__ DF det3(const V3<DF>& A, const V3<DF>& B, const V3<DF>& C) {
   const DF cx = B.y * C.z - B.z * C.y;
@@ -123,26 +86,6 @@ __device__ __forceinline__ bool df_root(const Batch& p, int64_t g, Scaled<DF>& s
   coefficients_from_edges(a, b, gg, s);
   return true;
 }
-
-// Ordering of normalised pairs (hi = the rounding of hi + lo, as every
-// operation above returns them): rounding is monotone, so hi1 < hi2 implies
-// hi1 + lo1 <= hi2 + lo2, and equal his compare by lo.
-__device__ __forceinline__ bool df_less(const DF& a, const DF& b) {
-  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
-}
-__device__ __forceinline__ DF df_min(const DF& a, const DF& b) { return df_less(b, a) ? b : a; }
-__device__ __forceinline__ DF df_max(const DF& a, const DF& b) { return df_less(a, b) ? b : a; }
-
-// Exact sign test v - t > 0 for a float t.  two_sum gives hi - t = s + r
-// exactly; when hi is within a factor 2 of t, r = 0 (Sterbenz) and the sign
-// of the rounded s + lo is the sign of the exact s + lo; otherwise |s| is far
-// above |r + lo| and decides alone.
-__device__ __forceinline__ bool df_gt(const DF& v, float t) {
-  float s, r;
-  two_sum(v.hi, -t, s, r);
-  return s + (r + v.lo) > 0.f;
-}
-__device__ __forceinline__ bool df_le(const DF& v, float t) { return !df_gt(v, t); }
 
 // Depth-0 decision from the double-float coefficients and their bound E
 // (outcomes as fp32_classify: 0 invalid, 1 valid, 2 refine, 3 undecided);
