@@ -1,19 +1,26 @@
 // Everything after the bulk pass, in one persistent cooperative launch:
-//  phase E  (FP32 form) the escalated elements that the FP32 pass left in
-//           the escalation list are redone in FP64 (element64.cuh);
-//  levels   refinement of undecided elements (Sec. 6, recursive_subdivision),
-//           breadth first, one level per grid-wide step;
+//  phase R  (FP32 form) refinement in FP32 of the elements the FP32 pass
+//           listed (refine32.cuh); elements whose signs FP32 cannot settle
+//           are listed for the FP64 redo;
+//  phase E  (FP32 form) the escalated elements the FP32 pass (or the
+//           double-float redo) left, and those of phase R, redone in FP64
+//           (element64.cuh);
 //  phase X0 elements whose root signs could not be certified: decided
 //           exactly at depth 0, or refined from their FP64 root box;
+//  levels   refinement of undecided elements (Sec. 6, recursive_subdivision),
+//           breadth first, one level per grid-wide step, each followed by
+//           phase XB, the exact check of the boxes an uncertain sign left
+//           open (exact_warp.cuh);
 //  phase F  verdicts of the refined elements;
 //  phase X  the full exact tier (exact.cuh) for what is left (coordinates
 //           outside the fast exact range, a full queue or list), only when
 //           some element needs it.
-// Grid-wide steps are separated by a bounded grid barrier.  Every count that
-// decides a branch is read after a barrier (or was written by an earlier
-// launch), so all blocks take the same branches; with nothing to do the
-// kernel returns at its first instructions.  The last block to finish folds
-// the batch counters into the statistics and resets them.
+// Grid-wide steps are separated by a bounded grid barrier (tail_barrier; a
+// block whose wait runs out stops its work and only joins the final fold).
+// Every count that decides a branch is read after a barrier (or was written
+// by an earlier launch), so all blocks take the same branches; with nothing
+// to do the kernel returns at its first instructions.  The last block to
+// finish folds the batch counters into the statistics and resets them.
 //
 // Refinement.  Level d holds boxes of depth d whose corners are certainly
 // positive and which are certainly not certified.  Each is split at 1/2
