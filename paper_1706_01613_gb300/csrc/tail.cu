@@ -589,7 +589,7 @@ uint64_t exact_work_words() {
   return static_cast<uint64_t>(exact_tier::kInts) * exact_tier::kLimbsMax * exact_tier::kWorkers;
 }
 
-// Cooperative (all blocks resident: the grid barrier) and, where the driver
+// Cooperative (all blocks resident: the grid barrier) and, where the CUDA driver
 // accepts it, programmatic (it may become resident while the bulk pass
 // finishes; tail_kernel starts with pdl_wait).  spin_limit = polls of the
 // grid barrier before it gives up (kSpinLimit by default).
