@@ -132,8 +132,10 @@ typedef struct {
 int hexval_config_default(hexval_config* cfg);
 
 /* Creates a handle on cfg->device and allocates all of its device scratch
- * (about 460 B x queue_capacity + 16 B x max_nodes + 4 B x max_batch + 39 MB
- * with the defaults: ~4.2 GB).  Returns HEXVAL_E_NOMEM if that fails. */
+ * (about 485 B x queue_capacity + 16 B x max_nodes + 4 B x max_batch + 40 MB,
+ * ~4.4 GB with the defaults; the FP32-filtered form adds about 225 B x
+ * queue_capacity + 32 B x max_batch, ~2.4 GB).  Returns HEXVAL_E_NOMEM if
+ * that fails. */
 int hexval_create(const hexval_config* cfg, hexval_handle* out);
 
 /* Frees the handle's scratch (synchronises its device). */
