@@ -101,9 +101,24 @@ static void build_T(void) {
   T_ready = 1;
 }
 
-/* Unit roundoff of binary64 and the bound constants (see the derivation in the
- * design notes): a J sample passes through <= 15 roundings, a Bezier
- * coefficient through <= 15 + 26, one subdivision level through <= 6. */
+/* Unit roundoff u of binary64 and the bound constants.  Standard forward
+ * error analysis (Higham, "Accuracy and Stability of Numerical Algorithms",
+ * ch. 3): a value built from sums and products in which every term passes
+ * through at most k roundings lies within gamma_k = k u / (1 - k u) times the
+ * same expression evaluated on absolute values of its exact value.  In
+ * jac_det the shape-function derivatives at the lattice points are 0, +-1/4,
+ * +-1/2 or +-1, so the products X * d are exact; a Jacobian entry then passes
+ * through 7 roundings (8 terms summed), a determinant term through 2 more (a
+ * product of three entries) and the signed sum of the 6 terms through 5
+ * more: <= 14 per J sample, bounded by 15 here.  A Bezier coefficient adds
+ * the dyadic weights of its row of Table t:Tb (exact products) and <= 26
+ * additions: with |c - c_exact| <= gamma_15 M, |b - b_exact| <= gamma_41
+ * sum |T| M.  One subdivision level forms each child coefficient by three
+ * de Casteljau passes of two averages each (the halvings are exact): <= 6
+ * roundings of a convex combination, so gamma_6 max |b| more.  K_C, K_B and
+ * K_SUB are 2 gamma_15, 2 gamma_41 and gamma_6 rounded up (the factor covers
+ * the 1 / (1 - k u) denominators); E_FLOOR covers the absolute errors of
+ * gradual underflow. */
 #define U64 (1.1102230246251565e-16) /* 2^-53 */
 #define K_C (32.0 * U64)             /* >= 2 * gamma_15 inflation */
 #define K_B (128.0 * U64)            /* >= 2 * gamma_41 inflation */
