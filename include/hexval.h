@@ -86,6 +86,20 @@ typedef struct {
                               2^24, well over a second); a small value is for
                               testing the timeout path */
   uint32_t reserved;       /* must be 0 */
+  /* work placement (tuning knobs; results do not depend on them): */
+  uint32_t esc_in_pass;    /* FP32 form: per batch, the first esc_in_pass FP32
+                              escalations are redone in FP64 inside the FP32
+                              pass by whole warps, the others by the tail
+                              kernel (default 4096) */
+  uint32_t refine_in_pass; /* FP32 form: per batch, the first refine_in_pass
+                              elements that need subdivision are redone and
+                              refined in FP64 inside the FP32 pass, the others
+                              refined in FP32 by the tail kernel (default 512) */
+  uint32_t tail_warp_items; /* a step of the tail kernel with at most this many
+                              items per warp runs one item per warp (latency),
+                              a larger one one item per thread (throughput);
+                              1..64 (default 8) */
+  uint32_t reserved2;      /* must be 0 */
 } hexval_config;
 
 /* options (tuning knobs; the same flags, and with HEXVAL_OPT_DFREDO the
@@ -140,6 +154,12 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out);
 
 /* Frees the handle's scratch (synchronises its device). */
 int hexval_destroy(hexval_handle h);
+
+/* Device bytes the handle holds (the scratch allocated by hexval_create),
+ * for callers that budget device memory, such as a server admitting
+ * requests next to a set of handles.  Not from the paper: bookkeeping of
+ * this library.  Host only; no synchronisation. */
+int hexval_scratch_bytes(hexval_handle h, uint64_t* bytes);
 
 /* Independent elements.
  *   corners: FP64, n_hex*24 values laid out as 24 planes [8][3][n_hex]: value
@@ -291,23 +311,31 @@ int hexval_profile_read(hexval_handle h, hexval_profile* out, int reset);
  * device memory pool is fixed after start-up).  The paper has no counterpart:
  * this is a packaging of hexval_check_soa (FP64 form) for such callers.
  *
- * It needs no handle.  Its scratch (refinement queue, refinement state,
- * exact-tier list and stacks, counters, status) is one static device array of
- * about 47 MB that every device which loads the library holds until the
- * process exits.  Limits: n_hex <= 16384 per call (larger calls return
- * HEXVAL_E_ARG and enqueue nothing); refinement levels of at most 16384
- * boxes (more boxes send the elements concerned to the exact tier);
- * max_depth 0..15.  Arguments as hexval_check_soa; status_bits, if not NULL,
- * is a device word that receives the call's device-status bits (1 bad index,
- * 2 queue or list full, 4 bounded wait gave up, 8 exact-tier range), written
- * in stream order.
+ * It needs no handle.  Its scratch (refinement queue with box positions,
+ * exact-check list, refinement state, exact-tier list and stacks, counters,
+ * status) is one static device array of about 48 MB that every device which
+ * loads the library holds until the process exits; the kernels and the
+ * arithmetic are those of hexval_check_soa on a FP64 handle, so flags
+ * (exact bit included) and bounds are the same whenever no refinement level
+ * exceeds the limit below on either side.  Limits: n_hex <= 16384 per
+ * call (larger calls return HEXVAL_E_ARG and enqueue nothing); refinement
+ * levels of at most 16384 boxes (more boxes send the elements concerned to
+ * the exact tier, which settles them exactly; the call's status then has
+ * bit 2 set although the flags are exact, unless the exact tier's list of
+ * 16384 elements fills too, which leaves those elements UNDECIDED);
+ * max_depth 0..15.  Arguments as hexval_check_soa; status_bits, if not
+ * NULL, is a device word that receives the call's device-status bits (1 bad
+ * index, 2 queue or list full, 4 bounded wait gave up, 8 exact-tier range),
+ * written in stream order.
  *
- * The first call on a device looks the array up (cudaGetSymbolAddress) and
- * zeroes its counters; make that first call before any stream capture.  All
- * calls share the array and it keeps the last call's contents: calls whose
- * work overlaps on the GPU (other streams, other host threads) race and must
- * be serialised by the caller.  No cudaMalloc, cudaFree or allocating
- * library routine is called. */
+ * Every call looks the array's device address up (cudaGetSymbolAddress);
+ * the first call on a device, and the first after a device reset that
+ * reloaded the library's module, also zeroes its counters on the caller's
+ * stream.  Make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents: calls whose work overlaps
+ * on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  No cudaMalloc, cudaFree or allocating library
+ * routine is called. */
 int hexval_check_soa_noalloc(int64_t n_hex, const double* corners, uint8_t* flags, double* bmin,
                              double* bmax, int32_t max_depth, uint32_t* status_bits,
                              void* stream);

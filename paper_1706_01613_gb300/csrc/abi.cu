@@ -63,6 +63,7 @@ struct hexval_ctx {
   Scratch s;
   void* blocks[48];
   int nblocks;
+  uint64_t scratch_bytes = 0;  // device bytes allocated by hexval_create
   Profiler prof;
   Replay replay;
 };
@@ -86,6 +87,7 @@ bool alloc(hexval_ctx* h, T** out, uint64_t count) {
     return false;
   }
   h->blocks[h->nblocks++] = p;
+  h->scratch_bytes += count * sizeof(T);
   *out = static_cast<T*>(p);
   return true;
 }
@@ -252,6 +254,9 @@ int hexval_config_default(hexval_config* cfg) {
   cfg->queue_capacity = 1ull << 23;
   cfg->max_nodes = 1ull << 24;
   cfg->exact_capacity = 1ull << 16;
+  cfg->esc_in_pass = hexval::kEscInPassDefault;
+  cfg->refine_in_pass = hexval::kR32InPassDefault;
+  cfg->tail_warp_items = hexval::kWarpItemsDefault;
   return HEXVAL_OK;
 }
 
@@ -264,7 +269,7 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
       cfg->exact_capacity > (1ull << 31) || cfg->max_nodes > (1ull << 31) ||
       (cfg->options & ~static_cast<uint32_t>(HEXVAL_OPT_PAIR32 | HEXVAL_OPT_PREFETCH | HEXVAL_OPT_DFREDO |
                                              HEXVAL_OPT_NO_REPLAY)) ||
-      cfg->reserved ||
+      cfg->reserved || cfg->reserved2 || cfg->tail_warp_items < 1 || cfg->tail_warp_items > 64 ||
       (cfg->bulk_threads != 0 && cfg->bulk_threads != 64 && cfg->bulk_threads != 128 &&
        cfg->bulk_threads != 256))
     return HEXVAL_E_ARG;
@@ -352,6 +357,9 @@ int hexval_check_soa(hexval_handle h, int64_t n_hex, const double* corners, uint
   p.pair32 = (h->cfg.options & HEXVAL_OPT_PAIR32) != 0;
   p.dfredo = (h->cfg.options & HEXVAL_OPT_DFREDO) != 0;
   p.bulk_threads = static_cast<int>(h->cfg.bulk_threads);
+  p.esc_in_pass = h->cfg.esc_in_pass;
+  p.r32_in_pass = h->cfg.refine_in_pass;
+  p.warp_items = h->cfg.tail_warp_items;
   p.flags = flags;
   p.bmin = bmin;
   p.bmax = bmax;
@@ -381,6 +389,9 @@ int hexval_check_indexed(hexval_handle h, int64_t n_nodes, const double* nodes, 
   p.prefetch32 = (h->cfg.options & HEXVAL_OPT_PREFETCH) != 0;
   p.dfredo = (h->cfg.options & HEXVAL_OPT_DFREDO) != 0;
   p.bulk_threads = static_cast<int>(h->cfg.bulk_threads);
+  p.esc_in_pass = h->cfg.esc_in_pass;
+  p.r32_in_pass = h->cfg.refine_in_pass;
+  p.warp_items = h->cfg.tail_warp_items;
   p.flags = flags;
   p.bmin = bmin;
   p.bmax = bmax;
@@ -524,6 +535,12 @@ int hexval_min_jacobian_indexed(hexval_handle h, int64_t n_nodes, const double* 
                              static_cast<cudaStream_t>(stream)) == cudaSuccess
              ? HEXVAL_OK
              : HEXVAL_E_CUDA;
+}
+
+int hexval_scratch_bytes(hexval_handle h, uint64_t* bytes) {
+  if (!h || !bytes) return HEXVAL_E_ARG;
+  *bytes = h->scratch_bytes;
+  return HEXVAL_OK;
 }
 
 int hexval_status(hexval_handle h, void* stream) {

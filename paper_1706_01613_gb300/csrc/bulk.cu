@@ -7,15 +7,15 @@
 //                  the refinement queue; uncertifiable ones the exact list.
 //  bulk32_kernel   the same in FP32 with a certified FP32 error bound; only
 //                  clear-cut elements are decided, the rest are escalated to
-//                  FP64: the first kEscInBulk of a batch right here, by the
+//                  FP64: the first esc_in_pass of a batch right here, by the
 //                  whole warp (warp_items.cuh), the others by the tail kernel.
 //  nodes32_kernel  FP64 nodes -> FP32 on the integer pipe, for the indexed
 //                  FP32 pass (one conversion per node instead of per corner).
 //
-// FP32 error bound (derivation in the design notes), u = 2^-24: with eps the
-// per-component error of the computed edge vectors (input rounding included)
-// and L the largest |component| among them, every sample and coefficient is
-// within 200 eps L^2 + 740 u L^3 of its exact value; the kernel uses
+// FP32 error bound, u = 2^-24 (element32.cuh): with eps the per-component
+// error of the computed edge vectors (input rounding included) and L the
+// largest |component| among them, every sample and coefficient is within
+// 200 eps L^2 + 740 u L^3 of its exact value; the kernel uses
 // 256 eps L^2 + 1024 u L^3 with eps = 2^-23 X + 2^-24 L, X >= |coordinates|.
 #include "element32.cuh"
 #include "warp_items.cuh"
@@ -30,14 +30,14 @@ constexpr int kBulk32Default = 128;  // default block of the FP32 kernels (measu
 
 // Escalation of a warp's uncertain elements (all 32 lanes call it; `want`
 // marks this lane's element e).  They are appended to the escalation list;
-// those that land in its first kEscInBulk positions are redone in FP64 here,
+// those that land in its first esc_in_pass positions are redone in FP64 here,
 // one at a time by the whole warp, on `sm` (kElemScratch doubles of shared
 // memory per warp); the others are written to the list for the tail kernel.
 __device__ __forceinline__ void escalate(const Batch& p, bool want, unsigned int e, double* sm) {
   if (!__any_sync(kFull, want)) return;
   const unsigned int pos = warp_append(&p.s.cnt->esc_count, want);
-  if (want && pos >= kEscInBulk) p.s.esc[pos] = e;  // capacity = batch size
-  unsigned int mine = __ballot_sync(kFull, want && pos < kEscInBulk);
+  if (want && pos >= p.esc_in_pass) p.s.esc[pos] = e;  // capacity = batch size
+  unsigned int mine = __ballot_sync(kFull, want && pos < p.esc_in_pass);
   while (mine) {
     const int src = __ffs(mine) - 1;
     mine &= mine - 1;
@@ -47,7 +47,7 @@ __device__ __forceinline__ void escalate(const Batch& p, bool want, unsigned int
 
 // Outputs of one element of the FP32 pass (all 32 lanes call it; outcomes of
 // fp32_classify, or 5 for a connectivity entry out of range): escalations go
-// to FP64 (escalate); of the elements to refine, the first kR32InBulk of the
+// to FP64 (escalate); of the elements to refine, the first r32_in_pass of the
 // batch are redone in FP64 here by the whole warp and the others are listed
 // for the FP32 refinement (their flag comes later); the rest get their
 // verdict here.
@@ -61,7 +61,7 @@ __device__ __forceinline__ void finish32(const Batch& p, bool act, int outcome, 
   bool r_here = false;
   if (__any_sync(kFull, want_r)) {  // rare: skip the list work otherwise
     rpos = warp_append(&S.cnt->r32_count, want_r);
-    r_here = want_r && rpos < kR32InBulk;  // FP64 redo right here
+    r_here = want_r && rpos < p.r32_in_pass;  // FP64 redo right here
     unsigned int mine = __ballot_sync(kFull, r_here);
     while (mine) {
       const int src = __ffs(mine) - 1;
@@ -106,6 +106,9 @@ __global__ void __launch_bounds__(kBulkThreads) bulk64_kernel(Batch p) {
 }
 
 // Decides what FP32 can decide; everything else is escalated to FP64.
+// At most 64 registers: this kernel relies on many resident warps to cover
+// its gather latency (measured faster than an 80-register build without
+// spills, at two-thirds of the warps).
 template <bool INDEXED>
 __global__ void __launch_bounds__(kBulkThreads, 4) bulk32_kernel(Batch p) {
   pdl_wait();
@@ -121,35 +124,27 @@ __global__ void __launch_bounds__(kBulkThreads, 4) bulk32_kernel(Batch p) {
     V3<float> Y[8];
     float X;  // bound on |coordinate| of the element
     if (!INDEXED) {
-      X = 0.f;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         Y[k].x = d2f_int(__ldg(p.soa + (3 * k + 0) * p.stride + g), bad);
         Y[k].y = d2f_int(__ldg(p.soa + (3 * k + 1) * p.stride + g), bad);
         Y[k].z = d2f_int(__ldg(p.soa + (3 * k + 2) * p.stride + g), bad);
-        X = fabsmax3(X, Y[k]);
       }
+      X = node_magnitude(Y);
     } else {
       const int4* c4 = reinterpret_cast<const int4*>(p.conn + 8 * g);
-      int4 c0 = __ldg(c4), c1 = __ldg(c4 + 1);
-      int id[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-      bool ok = true;
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        ok &= static_cast<uint32_t>(id[k]) < static_cast<uint64_t>(p.n_nodes);
-      if (!ok) {
+      const int4 c0 = __ldg(c4), c1 = __ldg(c4 + 1);
+      if (!ids_in_range(c0, c1, p.n_nodes)) {
         outcome = 5;
       } else {
+        const int id[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
         const float4* N = reinterpret_cast<const float4*>(S.node32);
-        float badw = 0.f;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          float4 h = __ldg(N + id[k]);
+          const float4 h = __ldg(N + id[k]);
           Y[k] = {h.x, h.y, h.z};
-          badw += h.w;
         }
-        bad = badw != 0.f;
-        X = fabsmax3(0.f, Y[0]);  // completed below with 3 L
+        X = fabsmax3(Y[0]);  // completed with 3 L; out-of-range nodes: +inf records
       }
     }
     if (outcome < 0) outcome = fp32_decide<INDEXED>(Y, X, bad, lo, hi);
@@ -182,7 +177,9 @@ inline size_t staged_bytes(int threads) {
   return static_cast<size_t>(threads) * 160 + scratch_bytes(threads);
 }
 
-__global__ void __launch_bounds__(kBulkThreads, 4) bulk32s_kernel(Batch p) {
+// Up to 85 registers (no spills): the staging hides the gather latency, so
+// this kernel needs fewer resident warps than bulk32_kernel.
+__global__ void __launch_bounds__(kBulkThreads, 3) bulk32s_kernel(Batch p) {
   pdl_wait();
   pdl_trigger();
   extern __shared__ float4 stage[];
@@ -208,10 +205,7 @@ __global__ void __launch_bounds__(kBulkThreads, 4) bulk32s_kernel(Batch p) {
   // if an entry is out of range (nothing is copied then)
   auto issue_nodes = [&](unsigned int e, const int4& c0, const int4& c1) {
     const int id[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      ok &= static_cast<uint32_t>(id[k]) < static_cast<uint64_t>(p.n_nodes);
+    const bool ok = ids_in_range(c0, c1, p.n_nodes);
     if (ok && e < n) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) cp_async16(my_nodes + 32 * k, N + id[k]);
@@ -231,12 +225,10 @@ __global__ void __launch_bounds__(kBulkThreads, 4) bulk32s_kernel(Batch p) {
     cp_wait_all();  // node records of tile j, connectivity of tile j+1
     const bool act = e < n, ok = ok_next;
     V3<float> Y[8];
-    float badw = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const float4 h = my_nodes[32 * k];
       Y[k] = {h.x, h.y, h.z};
-      badw += h.w;
     }
     c0 = my_conn[0];
     c1 = my_conn[T];
@@ -247,7 +239,7 @@ __global__ void __launch_bounds__(kBulkThreads, 4) bulk32s_kernel(Batch p) {
     int outcome = -1;
     float lo = 0.f, hi = 0.f;
     if (act) {
-      outcome = ok ? fp32_decide<true>(Y, fabsmax3(0.f, Y[0]), badw != 0.f, lo, hi) : 5;
+      outcome = ok ? fp32_decide<true>(Y, fabsmax3(Y[0]), false, lo, hi) : 5;
     }
     finish32(p, act, outcome, e, lo, hi, wsc);
   }
@@ -289,6 +281,55 @@ __device__ __forceinline__ void lane_of(const Scaled<F2>& s, Scaled<float>& q) {
   q.centre = lane<LANE>(s.centre);
 }
 
+template <int LANE>
+__device__ __forceinline__ V3<float> lane_v(const V3<F2>& v) {
+  return {lane<LANE>(v.x), lane<LANE>(v.y), lane<LANE>(v.z)};
+}
+
+template <int LANE>
+__device__ __forceinline__ float edge_magnitude_lane(const V3<F2> a[4], const V3<F2> b[4],
+                                                     const V3<F2> g[4]) {
+  V3<float> x[4], y[4], z[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    x[q] = lane_v<LANE>(a[q]);
+    y[q] = lane_v<LANE>(b[q]);
+    z[q] = lane_v<LANE>(g[q]);
+  }
+  return edge_magnitude(x, y, z);
+}
+
+// The FP32 decision of two elements with packed f32x2 arithmetic (lane 0 and
+// lane 1 of every F2 value): per element the same operations, roundings,
+// bound and outcome as fp32_decide.  X0 / X1 as for fp32_root.
+template <bool INDEXED>
+__device__ __forceinline__ void fp32_decide2(const V3<F2> Y[8], float X0, float X1, bool bad0,
+                                             bool bad1, int& r0, int& r1, float& lo0, float& hi0,
+                                             float& lo1, float& hi1) {
+  V3<F2> a[4], b[4], gg[4];
+  edges_from_nodes(Y, a, b, gg);
+  const float L0 = edge_magnitude_lane<0>(a, b, gg), L1 = edge_magnitude_lane<1>(a, b, gg);
+  if (INDEXED) {
+    X0 = fmaf(3.f, L0, X0);
+    X1 = fmaf(3.f, L1, X1);
+  }
+  const float eps0 = fmaf(0x1p-24f, L0, 0x1p-23f * X0), eps1 = fmaf(0x1p-24f, L1, 0x1p-23f * X1);
+  const float L20 = L0 * L0, L21 = L1 * L1;
+  const float E0 = fmaf(256.f * eps0, L20, 1024.f * 0x1p-24f * (L20 * L0)) * 1.0001f;
+  const float E1 = fmaf(256.f * eps1, L21, 1024.f * 0x1p-24f * (L21 * L1)) * 1.0001f;
+  bad0 |= !(L0 >= 0x1p-30f) || !(E0 < 0x1p100f);
+  bad1 |= !(L1 >= 0x1p-30f) || !(E1 < 0x1p100f);
+  Scaled<F2> s;
+  coefficients_from_edges(a, b, gg, s);
+  Scaled<float> q;
+  lane_of<0>(s, q);
+  r0 = fp32_classify(q, E0, lo0, hi0);
+  lane_of<1>(s, q);
+  r1 = fp32_classify(q, E1, lo1, hi1);
+  if (bad0) r0 = 3;
+  if (bad1) r1 = 3;
+}
+
 // The FP32 pass on two elements per thread (2t and 2t+1) with packed f32x2
 // arithmetic; decisions and bounds per element exactly as bulk32_kernel.
 constexpr int kPairThreads = 128;
@@ -311,85 +352,66 @@ __global__ void __launch_bounds__(kPairThreads, 4) bulk32x2_kernel(Batch p) {
     float X0 = 0.f, X1 = 0.f;
     if (!INDEXED) {
       const int64_t g0 = p.base + i0, g1 = p.base + j1;
+      V3<float> Y0[8], Y1[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const double* q = p.soa + (3 * k) * p.stride;
-        Y[k].x = F2(d2f_int(__ldg(q + g0), bad0), d2f_int(__ldg(q + g1), bad1));
-        Y[k].y = F2(d2f_int(__ldg(q + p.stride + g0), bad0), d2f_int(__ldg(q + p.stride + g1), bad1));
-        Y[k].z = F2(d2f_int(__ldg(q + 2 * p.stride + g0), bad0),
-                    d2f_int(__ldg(q + 2 * p.stride + g1), bad1));
-        X0 = fmaxf(X0, fmaxf(fabsf(Y[k].x.v.x), fmaxf(fabsf(Y[k].y.v.x), fabsf(Y[k].z.v.x))));
-        X1 = fmaxf(X1, fmaxf(fabsf(Y[k].x.v.y), fmaxf(fabsf(Y[k].y.v.y), fabsf(Y[k].z.v.y))));
+        Y0[k].x = d2f_int(__ldg(q + g0), bad0);
+        Y1[k].x = d2f_int(__ldg(q + g1), bad1);
+        Y0[k].y = d2f_int(__ldg(q + p.stride + g0), bad0);
+        Y1[k].y = d2f_int(__ldg(q + p.stride + g1), bad1);
+        Y0[k].z = d2f_int(__ldg(q + 2 * p.stride + g0), bad0);
+        Y1[k].z = d2f_int(__ldg(q + 2 * p.stride + g1), bad1);
+        Y[k].x = F2(Y0[k].x, Y1[k].x);
+        Y[k].y = F2(Y0[k].y, Y1[k].y);
+        Y[k].z = F2(Y0[k].z, Y1[k].z);
       }
+      X0 = node_magnitude(Y0);
+      X1 = node_magnitude(Y1);
     } else {
       const int4* c4 = reinterpret_cast<const int4*>(p.conn + 8 * (p.base + i0));
       int4 c0 = __ldg(c4), c1 = __ldg(c4 + 1);
       int4 c2 = act1 ? __ldg(c4 + 2) : c0, c3 = act1 ? __ldg(c4 + 3) : c1;
-      int id0[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-      int id1[8] = {c2.x, c2.y, c2.z, c2.w, c3.x, c3.y, c3.z, c3.w};
-      bool ok0 = true, ok1 = true;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        ok0 &= static_cast<uint32_t>(id0[k]) < static_cast<uint64_t>(p.n_nodes);
-        ok1 &= static_cast<uint32_t>(id1[k]) < static_cast<uint64_t>(p.n_nodes);
+      if (!ids_in_range(c0, c1, p.n_nodes)) {
+        out0 = 5;
+        c0 = c1 = make_int4(0, 0, 0, 0);  // node 0 exists (n_nodes >= 1)
       }
-      if (!ok0) out0 = 5;
-      if (!ok1) out1 = 5;
+      if (!ids_in_range(c2, c3, p.n_nodes)) {
+        out1 = 5;
+        c2 = c3 = make_int4(0, 0, 0, 0);
+      }
+      const int id0[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+      const int id1[8] = {c2.x, c2.y, c2.z, c2.w, c3.x, c3.y, c3.z, c3.w};
       const float4* N = reinterpret_cast<const float4*>(S.node32);
-      float bw0 = 0.f, bw1 = 0.f;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        float4 h0 = ok0 ? __ldg(N + id0[k]) : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 h1 = ok1 ? __ldg(N + id1[k]) : h0;
+        const float4 h0 = __ldg(N + id0[k]), h1 = __ldg(N + id1[k]);
         Y[k].x = F2(h0.x, h1.x);
         Y[k].y = F2(h0.y, h1.y);
         Y[k].z = F2(h0.z, h1.z);
-        bw0 += h0.w;
-        bw1 += h1.w;
       }
-      bad0 = bw0 != 0.f;
-      bad1 = bw1 != 0.f;
-      X0 = fmaxf(fabsf(Y[0].x.v.x), fmaxf(fabsf(Y[0].y.v.x), fabsf(Y[0].z.v.x)));
-      X1 = fmaxf(fabsf(Y[0].x.v.y), fmaxf(fabsf(Y[0].y.v.y), fabsf(Y[0].z.v.y)));
+      // completed with 3 L; out-of-range nodes: +inf records
+      X0 = max3f(fabsf(Y[0].x.v.x), fabsf(Y[0].y.v.x), fabsf(Y[0].z.v.x));
+      X1 = max3f(fabsf(Y[0].x.v.y), fabsf(Y[0].y.v.y), fabsf(Y[0].z.v.y));
     }
-    V3<F2> a[4], b[4], gg[4];
-    edges_from_nodes(Y, a, b, gg);
-    float L0 = 0.f, L1 = 0.f;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const V3<F2>* vs[3] = {&a[q], &b[q], &gg[q]};
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        L0 = fmaxf(L0, fmaxf(fabsf(vs[r]->x.v.x), fmaxf(fabsf(vs[r]->y.v.x), fabsf(vs[r]->z.v.x))));
-        L1 = fmaxf(L1, fmaxf(fabsf(vs[r]->x.v.y), fmaxf(fabsf(vs[r]->y.v.y), fabsf(vs[r]->z.v.y))));
-      }
-    }
-    if (INDEXED) {
-      X0 = fmaf(3.f, L0, X0);
-      X1 = fmaf(3.f, L1, X1);
-    }
-    float eps0 = fmaf(0x1p-24f, L0, 0x1p-23f * X0), eps1 = fmaf(0x1p-24f, L1, 0x1p-23f * X1);
-    float E0 = fmaf(256.f * eps0, L0 * L0, 1024.f * 0x1p-24f * (L0 * L0 * L0)) * 1.0001f;
-    float E1 = fmaf(256.f * eps1, L1 * L1, 1024.f * 0x1p-24f * (L1 * L1 * L1)) * 1.0001f;
-    bad0 |= !(L0 >= 0x1p-30f) || !(E0 < 0x1p100f);
-    bad1 |= !(L1 >= 0x1p-30f) || !(E1 < 0x1p100f);
-    Scaled<F2> s;
-    coefficients_from_edges(a, b, gg, s);
-    Scaled<float> q;
-    lane_of<0>(s, q);
-    int r0 = fp32_classify(q, E0, lo0, hi0);
-    lane_of<1>(s, q);
-    int r1 = fp32_classify(q, E1, lo1, hi1);
-    if (out0 < 0) out0 = bad0 ? 3 : r0;
-    if (out1 < 0) out1 = bad1 ? 3 : r1;
+    int r0, r1;
+    fp32_decide2<INDEXED>(Y, X0, X1, bad0, bad1, r0, r1, lo0, hi0, lo1, hi1);
+    if (out0 < 0) out0 = r0;
+    if (out1 < 0) out1 = r1;
   }
   finish32(p, act0, out0, i0, lo0, hi0, warp_scratch());
   finish32(p, act1, out1, i1, lo1, hi1, warp_scratch());
 }
 
-// FP64 node -> FP32 record {x, y, z, bad} (16 bytes, one vector load in the
-// bulk pass); bad = 1 marks a coordinate outside the FP32 range (elements
-// touching such a node are escalated).
+// FP64 node -> FP32 record {x, y, z, w} (16 bytes, one vector load in the
+// bulk pass).  A node with a coordinate outside the FP32 range gets
+// x = y = z = +inf and w = 1, which sends every element touching it to FP64
+// (element32.cuh).
+__device__ __forceinline__ float4 node_record(float x, float y, float z, bool bad) {
+  const float inf = __int_as_float(0x7f800000);
+  return bad ? make_float4(inf, inf, inf, 1.f) : make_float4(x, y, z, 0.f);
+}
+
 __global__ void __launch_bounds__(256) nodes32_kernel(const double* nodes, int64_t n_nodes,
                                                       float4* out) {
   pdl_trigger();
@@ -399,7 +421,7 @@ __global__ void __launch_bounds__(256) nodes32_kernel(const double* nodes, int64
   float x = d2f_int(__ldg(nodes + 3 * i), bad);
   float y = d2f_int(__ldg(nodes + 3 * i + 1), bad);
   float z = d2f_int(__ldg(nodes + 3 * i + 2), bad);
-  out[i] = make_float4(x, y, z, bad ? 1.f : 0.f);
+  out[i] = node_record(x, y, z, bad);
 }
 
 // Two nodes per thread with 16-byte loads (nodes 16-byte aligned).
@@ -414,13 +436,13 @@ __global__ void __launch_bounds__(256) nodes32x2_kernel(const double2* nodes, in
     bool bad0 = false, bad1 = false;
     float x0 = d2f_int(a.x, bad0), y0 = d2f_int(a.y, bad0), z0 = d2f_int(b.x, bad0);
     float x1 = d2f_int(b.y, bad1), y1 = d2f_int(c.x, bad1), z1 = d2f_int(c.y, bad1);
-    out[i] = make_float4(x0, y0, z0, bad0 ? 1.f : 0.f);
-    out[i + 1] = make_float4(x1, y1, z1, bad1 ? 1.f : 0.f);
+    out[i] = node_record(x0, y0, z0, bad0);
+    out[i + 1] = node_record(x1, y1, z1, bad1);
   } else {
     const double* q = reinterpret_cast<const double*>(nodes) + 3 * i;
     bool bad = false;
     float x = d2f_int(__ldg(q), bad), y = d2f_int(__ldg(q + 1), bad), z = d2f_int(__ldg(q + 2), bad);
-    out[i] = make_float4(x, y, z, bad ? 1.f : 0.f);
+    out[i] = node_record(x, y, z, bad);
   }
 }
 

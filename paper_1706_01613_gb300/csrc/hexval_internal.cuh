@@ -74,18 +74,19 @@ struct Counters {
   unsigned int pad[1];
 };
 
-// Escalations of the FP32 pass: the first kEscInBulk elements appended to
-// the escalation list of a batch are redone in FP64 by the FP32 pass itself
-// (one element at a time by a whole warp, on the FP64 unit that the FP32
-// pass leaves idle); their list entries stay unwritten.  Entries from
-// kEscInBulk on are written and redone by the tail kernel.
-constexpr unsigned int kEscInBulk = 4096;
-
-// Elements the FP32 pass finds to need subdivision: the first kR32InBulk of a
-// batch are redone in FP64 by the pass itself (and refined in FP64: for a
-// handful of elements that is cheaper than the FP32 refinement's own
-// steps), the others are refined in FP32 by the tail kernel (phase R).
-constexpr unsigned int kR32InBulk = 512;
+// Escalations of the FP32 pass: the first Batch::esc_in_pass elements
+// appended to the escalation list of a batch are redone in FP64 by the FP32
+// pass itself (one element at a time by a whole warp, on the FP64 unit that
+// the FP32 pass leaves idle); their list entries stay unwritten.  Entries
+// from esc_in_pass on are written and redone by the tail kernel.  Of the
+// elements the FP32 pass finds to need subdivision, the first
+// Batch::r32_in_pass are redone in FP64 by the pass itself (and refined in
+// FP64: for a handful of elements that is cheaper than the FP32 refinement's
+// own steps), the others are refined in FP32 by the tail kernel (phase R).
+// Defaults of the configuration:
+constexpr unsigned int kEscInPassDefault = 4096;
+constexpr unsigned int kR32InPassDefault = 512;
+constexpr unsigned int kWarpItemsDefault = 8;
 
 // In-warp FP64 refinement (warp_items.cuh): workspaces per batch and boxes
 // per level of one workspace.
@@ -124,7 +125,7 @@ struct Scratch {
   // exact tier
   uint32_t* exact_list;
   uint64_t exact_cap;
-  uint32_t* exact_work;  // per-worker stacks (exact.cu)
+  uint32_t* exact_work;  // per-worker stacks (exact.cuh)
   uint64_t exact_work_words;
   // FP32 copies of the nodes for the indexed path: hi, lo (x, y, z each)
   float* node32;
@@ -169,6 +170,9 @@ struct Batch {
   int bulk_threads;  // block size of the bulk kernels (0: default)
   int prefetch32;    // indexed FP32 pass on a persistent grid with prefetch
   int dfredo;        // FP32 form: escalations redone in double-float first
+  unsigned int esc_in_pass;  // FP32 escalations of a batch redone in FP64 by the FP32 pass
+  unsigned int r32_in_pass;  // elements to refine redone in FP64 by the FP32 pass
+  unsigned int warp_items;   // tail: warp-per-item steps up to this many items per warp
   // outputs (indexed by base + e)
   uint8_t* flags;
   double* bmin;

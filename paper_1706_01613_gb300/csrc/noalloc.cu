@@ -5,17 +5,18 @@
 // or in a process whose allocator is locked after start-up).
 //
 // It launches the same kernels as hexval_check_soa with a FP64 handle
-// (bulk64, then the tail with the exact tier), but their scratch -- refinement queue, per-element
-// refinement state, exact-tier list and stacks, counters, statistics and
-// status -- lives in one file-scope static device array of fixed size,
-// instead of memory allocated by hexval_create.  The caller passes only the
-// inputs and the outputs.
+// (bulk64, then the tail with the exact box check and the exact tier), but
+// their scratch -- refinement queue with box positions, exact-check list,
+// per-element refinement state, exact-tier list and stacks, counters,
+// statistics and status -- lives in one file-scope static device array of
+// fixed size, instead of memory allocated by hexval_create.  The caller
+// passes only the inputs and the outputs.
 //
 // Limits: at most kNoallocMaxHex elements per call, a refinement queue of
 // kNoallocMaxHex boxes per level (a level that would need more sends the
 // elements concerned to the exact tier, whose list holds kNoallocMaxHex
 // elements), depth cap 0..15.  The static array takes kScratchBytes (about
-// 47 MB) on every device that loads the library, until the process exits.
+// 48 MB) on every device that loads the library, until the process exits.
 #include <cstring>
 #include <mutex>
 
@@ -32,7 +33,12 @@ constexpr uint64_t kOffQcoef0 = 0;
 constexpr uint64_t kOffQcoef1 = align256(kOffQcoef0 + 27 * kCap * sizeof(double));
 constexpr uint64_t kOffQslot0 = align256(kOffQcoef1 + 27 * kCap * sizeof(double));
 constexpr uint64_t kOffQslot1 = align256(kOffQslot0 + kCap * sizeof(uint32_t));
-constexpr uint64_t kOffElem = align256(kOffQslot1 + kCap * sizeof(uint32_t));
+constexpr uint64_t kOffQpos0 = align256(kOffQslot1 + kCap * sizeof(uint32_t));
+constexpr uint64_t kOffQpos1 = align256(kOffQpos0 + kCap * sizeof(uint64_t));
+constexpr uint64_t kOffXbSlot = align256(kOffQpos1 + kCap * sizeof(uint64_t));
+constexpr uint64_t kOffXbQi = align256(kOffXbSlot + hexval::kXbCap * sizeof(uint32_t));
+constexpr uint64_t kOffXbPos = align256(kOffXbQi + hexval::kXbCap * sizeof(uint32_t));
+constexpr uint64_t kOffElem = align256(kOffXbPos + hexval::kXbCap * sizeof(uint64_t));
 constexpr uint64_t kOffState = align256(kOffElem + kCap * sizeof(uint32_t));
 constexpr uint64_t kOffLev = align256(kOffState + kCap * sizeof(uint32_t));
 constexpr uint64_t kOffE0 = align256(kOffLev + kCap * sizeof(uint32_t));
@@ -54,20 +60,23 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 unsigned char* g_addr[kMaxDevices] = {};
 
-// Device address of `scratch` on the current device, looked up once per
-// device (the first call on a device does it).
-int scratch_address(int dev, unsigned char** out) {
+// Device address of `scratch` on the current device.  It is looked up on
+// every call (a host-side query); when it differs from the one seen before
+// on this device (the first call, or a new context after a device reset
+// reloaded the module) the counters are zeroed on the caller's stream, ahead
+// of the call's kernels.  Later calls find them at zero: every call's tail
+// kernel resets them.
+int scratch_address(int dev, cudaStream_t st, unsigned char** out) {
   if (dev < 0 || dev >= kMaxDevices) return HEXVAL_E_ARG;
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, scratch) != cudaSuccess || !ptr) {
+    cudaGetLastError();
+    return HEXVAL_E_CUDA;
+  }
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_addr[dev]) {
-    void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return HEXVAL_E_CUDA;
-    }
-    // the counters must start at zero; later calls leave them at zero
-    if (cudaMemset(static_cast<unsigned char*>(ptr) + kOffCnt, 0,
-                   kOffExactWork - kOffCnt) != cudaSuccess) {
+  if (g_addr[dev] != ptr) {
+    if (cudaMemsetAsync(static_cast<unsigned char*>(ptr) + kOffCnt, 0, kOffExactWork - kOffCnt,
+                        st) != cudaSuccess) {
       cudaGetLastError();
       return HEXVAL_E_CUDA;
     }
@@ -88,10 +97,10 @@ extern "C" int hexval_check_soa_noalloc(int64_t n_hex, const double* corners, ui
   if (hexval::exact_work_words() != kExactWorkWords) return HEXVAL_E_CUDA;  // layout guard
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return HEXVAL_E_CUDA;
-  unsigned char* base = nullptr;
-  int rc = scratch_address(dev, &base);
-  if (rc != HEXVAL_OK) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned char* base = nullptr;
+  int rc = scratch_address(dev, st, &base);
+  if (rc != HEXVAL_OK) return rc;
   // status of this call starts clean (the array keeps the last call's contents)
   if (cudaMemsetAsync(base + kOffStatus, 0, sizeof(uint32_t), st) != cudaSuccess)
     return HEXVAL_E_CUDA;
@@ -106,12 +115,21 @@ extern "C" int hexval_check_soa_noalloc(int64_t n_hex, const double* corners, ui
     p.bmin = bmin;
     p.bmax = bmax;
     p.max_depth = max_depth;
+    p.esc_in_pass = hexval::kEscInPassDefault;
+    p.r32_in_pass = hexval::kR32InPassDefault;
+    p.warp_items = hexval::kWarpItemsDefault;
     hexval::Scratch& s = p.s;
     s.qcoef[0] = reinterpret_cast<double*>(base + kOffQcoef0);
     s.qcoef[1] = reinterpret_cast<double*>(base + kOffQcoef1);
     s.qslot[0] = reinterpret_cast<uint32_t*>(base + kOffQslot0);
     s.qslot[1] = reinterpret_cast<uint32_t*>(base + kOffQslot1);
+    s.qpos[0] = reinterpret_cast<uint64_t*>(base + kOffQpos0);
+    s.qpos[1] = reinterpret_cast<uint64_t*>(base + kOffQpos1);
     s.qcap = kCap;
+    s.xb_slot = reinterpret_cast<uint32_t*>(base + kOffXbSlot);
+    s.xb_qi = reinterpret_cast<uint32_t*>(base + kOffXbQi);
+    s.xb_pos = reinterpret_cast<uint64_t*>(base + kOffXbPos);
+    s.xb_cap = hexval::kXbCap;
     s.slot_elem = reinterpret_cast<uint32_t*>(base + kOffElem);
     s.slot_state = reinterpret_cast<uint32_t*>(base + kOffState);
     s.slot_lev = reinterpret_cast<uint32_t*>(base + kOffLev);

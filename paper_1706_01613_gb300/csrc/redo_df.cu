@@ -1,5 +1,5 @@
 // Double-float redo of the FP32 form's escalations (HEXVAL_OPT_DFREDO): the
-// escalation list entries the FP32 pass leaves (beyond the first kEscInBulk,
+// escalation list entries the FP32 pass leaves (beyond the first esc_in_pass,
 // which it redoes in FP64 itself) are recomputed one per thread in
 // double-float (element_df.cuh), about 44 bits at FP32 throughput; what the
 // redo decides at depth 0 (valid or invalid) is final, and the rest (a sign
@@ -45,8 +45,8 @@ __global__ void __launch_bounds__(kRedoThreads, 4) redo_df_kernel(Batch p) {
   pdl_trigger();
   const Scratch& S = p.s;
   const unsigned int n_list = ldcg(&S.cnt->esc_count);
-  const unsigned int n = n_list > kEscInBulk ? n_list - kEscInBulk : 0u;
-  const uint32_t* esc = S.esc + kEscInBulk;
+  const unsigned int n = n_list > p.esc_in_pass ? n_list - p.esc_in_pass : 0u;
+  const uint32_t* esc = S.esc + p.esc_in_pass;
   const unsigned int stride = gridDim.x * blockDim.x;
   // uniform trip count per warp: blockDim.x is a multiple of 32
   for (unsigned int i0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); i0 < n; i0 += stride) {

@@ -28,13 +28,13 @@ __device__ __forceinline__ void split5f(float p0, float p1, float p2, float q[5]
 }
 
 // Root box of the i-th element left in the refinement list (list entry
-// kR32InBulk + i; slot i, box i of level 0): the FP32
+// r32_in_pass + i; slot i, box i of level 0): the FP32
 // coefficients recomputed exactly as the FP32 pass computed them, with their
 // bound.  Slots beyond the queue capacity are marked for the FP64 redo.
 __device__ __forceinline__ void root32(const Batch& p, bool act, unsigned int i) {
   if (!act) return;
   const Scratch& S = p.s;
-  const uint32_t e = ldcg(S.r32 + kR32InBulk + i);
+  const uint32_t e = ldcg(S.r32 + p.r32_in_pass + i);
   V3<float> Y[8];
   float X, E = 0.f, lo = 0.f, hi = 0.f;
   bool bad;

@@ -357,9 +357,9 @@ __device__ HEXVAL_TAIL_INLINE void fp64_item(const Batch& p, bool act, uint32_t 
   fp64_element(p, act, e);
 }
 
-// Steps with at most this many items per warp use the warp-cooperative
-// routines (latency), larger ones one item per thread (throughput).
-constexpr unsigned int kWarpItemsMax = 8;
+// Steps with at most Batch::warp_items items per warp use the
+// warp-cooperative routines (latency), larger ones one item per thread
+// (throughput).
 
 // Items dealt to warps one at a time, round robin over the blocks first.
 #define FOR_EACH_WARP_ITEM(n, i)                                                    \
@@ -422,7 +422,7 @@ __device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned in
     }
     if (t == 0) {
       const unsigned int nr = ldcg(&C->r32_count);
-      const unsigned int nr_here = nr < kR32InBulk ? nr : kR32InBulk;
+      const unsigned int nr_here = nr < p.r32_in_pass ? nr : p.r32_in_pass;
       atomicAdd(&st->elements, static_cast<unsigned long long>(p.n));
       atomicAdd(&st->escalated_fp64, static_cast<unsigned long long>(ldcg(&C->esc_count)) +
                                          ldcg(&C->esc2_count) + nr_here);
@@ -445,15 +445,15 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
   pdl_wait();
   const Scratch& S = p.s;
   Counters* C = S.cnt;
-  // escalation list entries [kEscInBulk, n_list) are left for this kernel,
+  // escalation list entries [esc_in_pass, n_list) are left for this kernel,
   // or, after the double-float redo, the esc3 list it leaves
   const unsigned int n_list = from_list ? ldcg(&C->esc_count) : 0u;
   const unsigned int n_esc = !from_list ? 0u
                              : p.dfredo ? ldcg(&C->esc3_count)
-                                        : (n_list > kEscInBulk ? n_list - kEscInBulk : 0u);
-  // refinement list entries [kR32InBulk, n_rl) are left for this kernel
+                                        : (n_list > p.esc_in_pass ? n_list - p.esc_in_pass : 0u);
+  // refinement list entries [r32_in_pass, n_rl) are left for this kernel
   const unsigned int n_rl = from_list ? ldcg(&C->r32_count) : 0u;
-  const unsigned int n_r = n_rl > kR32InBulk ? n_rl - kR32InBulk : 0u;
+  const unsigned int n_r = n_rl > p.r32_in_pass ? n_rl - p.r32_in_pass : 0u;
   if (n_esc == 0 && n_r == 0 && ldcg(&C->level_count[0]) == 0 && ldcg(&C->exact_count) == 0) {
     // nothing left: every block reads only counters that are, or become,
     // zero here, so block 0 may end the batch at once
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
   static_assert(exact_tier::kFastWords <= 2 * kWarpScratch, "warp scratch too small");
   static_assert(27 * exact_tier::kBoxWords <= 2 * kWarpScratch, "warp scratch too small");
   double* mysm = wsm[threadIdx.x >> 5];
-  const unsigned int warp_items = kWarpItemsMax * gridDim.x * (blockDim.x >> 5);
+  const unsigned int warp_items = p.warp_items * gridDim.x * (blockDim.x >> 5);
   unsigned int epoch = 0;
   unsigned int n_esc2 = 0;
   // false once a grid barrier timed out: the block then skips to the end
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
     if (go) n_esc2 = ldcg(&C->esc2_count);
   }
   if (go && n_esc + n_esc2) {  // phase E: list entries, then the FP32 refinement's
-    const uint32_t* esc = p.dfredo ? S.esc3 : S.esc + kEscInBulk;
+    const uint32_t* esc = p.dfredo ? S.esc3 : S.esc + p.esc_in_pass;
     const unsigned int n_e = n_esc + n_esc2;
     if (n_e <= warp_items) {
       FOR_EACH_WARP_ITEM(n_e, i)

@@ -32,7 +32,7 @@ EXPORTS = ("hexval_config_default", "hexval_create", "hexval_destroy", "hexval_c
            "hexval_profile_read", "hexval_check_soa_noalloc", "hexval_check_quads",
            "hexval_check_quads_indexed", "hexval_corner_quality",
            "hexval_corner_quality_indexed", "hexval_compact", "hexval_min_jacobian",
-           "hexval_min_jacobian_indexed", "hexval_strerror")
+           "hexval_min_jacobian_indexed", "hexval_strerror", "hexval_scratch_bytes")
 PHASES = ("nodes32", "bulk32", "bulk64", "tail", "-", "redo_df", "-", "-")
 
 
@@ -42,7 +42,9 @@ class Config(ctypes.Structure):
                 ("max_batch", ctypes.c_uint64), ("queue_capacity", ctypes.c_uint64),
                 ("max_nodes", ctypes.c_uint64), ("exact_capacity", ctypes.c_uint64),
                 ("options", ctypes.c_uint32), ("bulk_threads", ctypes.c_uint32),
-                ("spin_limit", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("spin_limit", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("esc_in_pass", ctypes.c_uint32), ("refine_in_pass", ctypes.c_uint32),
+                ("tail_warp_items", ctypes.c_uint32), ("reserved2", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -88,6 +90,7 @@ def load(build_if_missing=False):
     lib.hexval_check_soa.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     lib.hexval_check_indexed.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, vp]
     lib.hexval_status.argtypes = [vp, vp]
+    lib.hexval_scratch_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     lib.hexval_get_stats.argtypes = [vp, ctypes.POINTER(Stats), ctypes.c_int, vp]
     lib.hexval_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.hexval_profile_read.argtypes = [vp, ctypes.POINTER(Profile), ctypes.c_int]
@@ -139,8 +142,9 @@ class Validator:
     precision: "fp64" (plain FP64 bulk pass) or "fp32" (FP32-filtered bulk
     pass with certified escalation).  The remaining keywords override fields
     of the default configuration (max_depth, queue_capacity, max_batch,
-    max_nodes, exact_capacity, bulk_threads, options = OPT_* bits: PAIR32,
-    PREFETCH, DFREDO, NO_REPLAY).  Repeated identical check calls are
+    max_nodes, exact_capacity, bulk_threads, esc_in_pass, refine_in_pass,
+    tail_warp_items, options = OPT_* bits: PAIR32, PREFETCH, DFREDO,
+    NO_REPLAY).  Repeated identical check calls are
     replayed from a CUDA graph unless NO_REPLAY is set."""
 
     def __init__(self, precision="fp64", max_depth=8, device=None, **caps):
@@ -362,6 +366,12 @@ class Validator:
         else:
             self.check_indexed(dev[0], dev[1], out=(flags, None, None), stream=stream)
         return flags.to("cpu")
+
+    def scratch_bytes(self):
+        """Device bytes held by this handle's scratch."""
+        out = ctypes.c_uint64()
+        _check(self._lib.hexval_scratch_bytes(self._h, ctypes.byref(out)), "hexval_scratch_bytes")
+        return int(out.value)
 
     def status(self, stream=None):
         """Synchronises and returns (and clears) the sticky device status."""

@@ -5,9 +5,12 @@ a fixed set of slots; each slot owns one library handle (its refinement
 queue and exact-tier scratch stay on the device) and one CUDA stream.  A
 request is admitted as soon as a slot is free and its device footprint
 (inputs + outputs) fits in the HBM budget next to the requests already in
-flight; admitted requests overlap on the device (copy in, bulk pass, tail,
+flight; the slots' own scratch (refinement queues, exact-tier stacks, node
+records: fixed when the handles are created) is charged to the budget
+first.  Admitted requests overlap on the device (copy in, bulk pass, tail,
 copy out, all on the slot's stream).  Admission is first come, first served;
-a request larger than the whole budget is rejected.
+a request larger than what the budget leaves next to the slots' scratch is
+rejected.
 
 Latency = GPU completion time (an event on the slot's stream, read against
 an event recorded when the run started) minus the arrival time.
@@ -24,28 +27,43 @@ import numpy as np
 
 
 class Request:
-    __slots__ = ("id", "kind", "arrays", "n", "arrival", "bytes", "result", "done", "admitted")
+    __slots__ = ("id", "kind", "arrays", "source", "n", "arrival", "bytes", "result", "done",
+                 "admitted")
 
-    def __init__(self, rid, kind, arrays, n, arrival):
+    def __init__(self, rid, kind, arrays, n, arrival, source=None):
         self.id = rid
         self.kind = kind          # "soa": (corners,), "indexed": (nodes, conn)
         self.arrays = arrays      # host arrays (pinned torch tensors for the GPU executor)
+        # or, for SoA requests cut from a pool, (pool planes (8, 3, N), offset):
+        # the executor copies the n columns of each plane straight to the
+        # device, so no per-request host copy is made
+        self.source = source
         self.n = int(n)           # elements
         self.arrival = float(arrival)
-        in_bytes = sum(int(a.numel() * a.element_size()) if hasattr(a, "numel")
-                       else int(a.nbytes) for a in arrays)
+        if arrays is not None:
+            in_bytes = sum(int(a.numel() * a.element_size()) if hasattr(a, "numel")
+                           else int(a.nbytes) for a in arrays)
+        else:
+            in_bytes = 192 * self.n
         self.bytes = in_bytes + 17 * self.n  # + flags, bmin, bmax
         self.result = None
         self.done = None
         self.admitted = None
 
+    def host_arrays(self):
+        """The request's inputs as contiguous host arrays."""
+        if self.arrays is not None:
+            return self.arrays
+        X, off = self.source
+        return (X[:, :, off:off + self.n].contiguous(),)
+
 
 class Scheduler:
     """FIFO admission under a slot count and a byte budget."""
 
-    def __init__(self, slots, budget_bytes):
+    def __init__(self, slots, budget_bytes, reserved_bytes=0):
         self.free_slots = list(range(slots))
-        self.budget = int(budget_bytes)
+        self.budget = int(budget_bytes) - int(reserved_bytes)  # left for requests
         self.in_use = 0
         self.pending = collections.deque()
         self.rejected = []
@@ -76,8 +94,10 @@ class Scheduler:
 
 def run_stream(requests, executor, slots, budget_bytes, now=time.perf_counter, idle=None):
     """Serves `requests` (sorted by arrival, times in seconds from the start)
-    on `executor`; returns the scheduler (for the rejected list)."""
-    sched = Scheduler(slots, budget_bytes)
+    on `executor`; returns the scheduler (for the rejected list).  The
+    executor's fixed device memory (`fixed_bytes`, the slots' scratch) is
+    charged to the budget before any request."""
+    sched = Scheduler(slots, budget_bytes, getattr(executor, "fixed_bytes", 0))
     order = sorted(requests, key=lambda r: r.arrival)
     t0 = now()
     executor.start()
@@ -103,16 +123,28 @@ def run_stream(requests, executor, slots, budget_bytes, now=time.perf_counter, i
 
 
 def latency_summary(requests):
-    lat = np.array([r.done - r.arrival for r in requests if r.done is not None])
-    hexes = sum(r.n for r in requests if r.done is not None)
+    """p50 / p99 / max latency over the completed requests, throughput over
+    the span from the first arrival to the last completion, and p50 / p99
+    per size decade ([10^k, 10^(k+1)) elements)."""
+    done = [r for r in requests if r.done is not None]
+    lat = np.array([r.done - r.arrival for r in done])
+    hexes = sum(r.n for r in done)
     if not len(lat):
         return {}
-    span = max(r.done for r in requests if r.done is not None) - min(r.arrival for r in requests)
+    span = max(r.done for r in done) - min(r.arrival for r in requests)
+    by_size = {}
+    dec = np.array([int(math.floor(math.log10(max(1, r.n)))) for r in done])
+    for k in sorted(set(dec.tolist())):
+        sel = lat[dec == k]
+        by_size["1e%d-1e%d" % (k, k + 1)] = {
+            "requests": int(len(sel)), "p50_ms": float(np.percentile(sel, 50) * 1e3),
+            "p99_ms": float(np.percentile(sel, 99) * 1e3)}
     return {"requests": int(len(lat)), "hexes": int(hexes),
             "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "max_ms": float(lat.max() * 1e3),
-            "hex_per_s": float(hexes / span) if span > 0 else None}
+            "hex_per_s": float(hexes / span) if span > 0 else None,
+            "by_size": by_size}
 
 
 class GpuExecutor:
@@ -125,6 +157,7 @@ class GpuExecutor:
         self.v = [hv.Validator(precision=precision, max_depth=max_depth, **caps)
                   for _ in range(slots)]
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.fixed_bytes = sum(v.scratch_bytes() for v in self.v)
         self.events = [None] * slots
         self.buffers = [None] * slots
         self.t0 = None
@@ -141,7 +174,14 @@ class GpuExecutor:
         torch = self.torch
         s = self.streams[slot]
         with torch.cuda.stream(s):
-            if req.kind == "soa":
+            if req.kind == "soa" and req.source is not None:
+                X, off = req.source
+                d = torch.empty((8, 3, req.n), dtype=X.dtype, device="cuda")
+                rows, src = d.view(24, req.n), X.view(24, X.shape[2])
+                for r in range(24):  # each plane's columns are contiguous
+                    rows[r].copy_(src[r, off:off + req.n], non_blocking=True)
+                dev = (d,)
+            elif req.kind == "soa":
                 X = req.arrays[0]
                 dev = (X.to("cuda", non_blocking=True),)
             else:
@@ -209,10 +249,7 @@ class Pool:
             hi = int(self.node_hi[n - 1]) + 1
             return Request(rid, "indexed", (self.nodes[:hi], self.conn[:n]), n, arrival)
         off = int(offset) % max(1, self.max_n - n + 1)
-        X = self.soa[kind]
-        dst = torch.empty((8, 3, n), dtype=torch.float64, pin_memory=True)
-        dst.copy_(X[:, :, off:off + n])
-        return Request(rid, "soa", (dst,), n, arrival)
+        return Request(rid, "soa", None, n, arrival, source=(self.soa[kind], off))
 
 
 def poisson_stream(pool, n_requests, rate, seed, size_min=100, size_max=10_000_000):

@@ -66,13 +66,31 @@ def structured_grid(nx=128, ny=None, nz=None, sigma=0.15, seed=None):
     return nodes, conn
 
 
+def _per_element(fn, *arrays, chunk=1 << 18):
+    """fn applied to consecutive chunks of the leading axis, on the host's
+    cores (the random numbers are drawn beforehand, and fn works element by
+    element, so the result is the same as one call)."""
+    import concurrent.futures as cf
+    import os
+    n = arrays[0].shape[0]
+    if n <= chunk:
+        return fn(*arrays)
+    parts = [slice(i, min(n, i + chunk)) for i in range(0, n, chunk)]
+    with cf.ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        out = list(ex.map(lambda sl: fn(*(a[sl] for a in arrays)), parts))
+    if isinstance(out[0], tuple):
+        return tuple(np.concatenate([o[k] for o in out]) for k in range(len(out[0])))
+    return np.concatenate(out)
+
+
 def _random_rotations(rng, n):
     G = rng.normal(size=(n, 3, 3))
-    Q, R = np.linalg.qr(G)
+    Q, R = _per_element(np.linalg.qr, G)
     d = np.sign(np.diagonal(R, axis1=1, axis2=2))
     d[d == 0] = 1.0
     Q = Q * d[:, None, :]
-    det = np.linalg.det(Q)
+    # orientation of the orthogonal Q (det = +-1): sign of the triple product
+    det = np.einsum("ni,ni->n", Q[:, :, 0], np.cross(Q[:, :, 1], Q[:, :, 2]))
     Q[det < 0, :, 0] *= -1.0  # proper rotations only
     return Q
 
@@ -118,7 +136,7 @@ def affine_mixture(n, seed=None, frac_degenerate=0.05, frac_inverted=0.05, r_max
     # their plane is sum_d |x_d - C_kd| = 1, and the mirror image of C_k in it
     # is C_k + (4/3) (centre - C_k)
     ref[idx, corner[idx]] = ck + (4.0 / 3.0) * (centre - ck)
-    X = np.einsum("nij,nkj->nki", A, ref) + t[:, None, :]
+    X = _per_element(lambda a, c: np.einsum("nij,nkj->nki", a, c), A, ref) + t[:, None, :]
     return np.ascontiguousarray(X.transpose(1, 2, 0)), kind, r
 
 

@@ -1,10 +1,14 @@
 """Autotuner for the launch configuration of the validity check.
 
 For a workload shape (precision, input kind, size) it times every candidate
-configuration of the handle (FP32 bulk pass scalar, staged or packed
-f32x2; bulk block size; then the double-float redo of escalations on the
-winner) on a sample input through the C ABI, with CUDA events on the
-launch stream, and keeps the fastest.  Results are cached per device name in
+launch configuration of the handle (FP32 bulk pass scalar, staged or packed
+f32x2; bulk block size; for the FP64 form the block size), re-times the
+leaders, then tries on the winner the double-float redo of escalations
+(FP32 form) and, one knob at a time, the placement of the uneven work: how
+many FP32 escalations and elements to refine the bulk pass keeps for itself
+(esc_in_pass, refine_in_pass) and the tail kernel's threshold between
+one item per warp and one per thread (tail_warp_items).  Timing is on a
+sample input through the C ABI, with CUDA events on the launch stream.  Results are cached per device name in
 a JSON file (default ~/.cache/hexval/tune.json, or $HEXVAL_TUNE_CACHE) so a
 shape is tuned once.
 
@@ -21,8 +25,16 @@ CACHE = os.environ.get("HEXVAL_TUNE_CACHE",
                        os.path.join(os.path.expanduser("~"), ".cache", "hexval", "tune.json"))
 
 
+# placement knobs tried one at a time on the winning launch configuration
+# (the first value of each list is the library default)
+KNOBS = {"fp32": [("esc_in_pass", (4096, 0, 1024, 16384)),
+                  ("refine_in_pass", (512, 0, 4096)),
+                  ("tail_warp_items", (8, 2, 32))],
+         "fp64": [("tail_warp_items", (8, 2, 32))]}
+
+
 def candidates(precision):
-    """Configurations to try (keyword arguments of hexval.Validator)."""
+    """Launch configurations to try (keyword arguments of hexval.Validator)."""
     out = []
     for bt in (64, 128, 256):
         out.append(dict(options=0, bulk_threads=bt))
@@ -113,6 +125,15 @@ def best_config(precision, kind, n, dev_inputs, cache=CACHE, retune=False, reps=
         results.append((ms, dfr))
         if ms < best_ms:
             best_ms, best = ms, dfr
+    best = dict(best)
+    for name, values in KNOBS[precision]:
+        best.setdefault(name, values[0])
+        for val in values[1:]:
+            trial = dict(best, **{name: val})
+            ms = time_config(trial, precision, kind, dev_inputs, reps=3 * reps, **caps)
+            results.append((ms, trial))
+            if ms < best_ms:
+                best_ms, best = ms, trial
     data[key] = {"config": best, "ms": best_ms,
                  "all": [{"config": c, "ms": m} for m, c in results],
                  "final": [{"config": c, "ms": m} for m, c in final]}

@@ -105,3 +105,12 @@ def test_options_outside_the_known_bits_are_refused(lib):
     bad.reserved = 1
     assert lib.hexval_create(ctypes.byref(bad), ctypes.byref(ctypes.c_void_p())) == -1
     assert hv.default_config().spin_limit == 0  # the default budget
+    for field, val in (("reserved2", 1), ("tail_warp_items", 0), ("tail_warp_items", 65)):
+        bad = hv.default_config()
+        setattr(bad, field, val)
+        assert lib.hexval_create(ctypes.byref(bad), ctypes.byref(ctypes.c_void_p())) == -1
+
+
+def test_placement_defaults():
+    cfg = hv.default_config()
+    assert (cfg.esc_in_pass, cfg.refine_in_pass, cfg.tail_warp_items) == (4096, 512, 8)

@@ -32,7 +32,8 @@ def test_mix_equals_alone(precision):
     alone = hv.Validator(precision=precision, max_depth=8, **caps)
     rng = np.random.default_rng(5)
     for r in reqs:
-        dev = [a.cuda() for a in r.arrays]
+        host = r.host_arrays()
+        dev = [a.cuda() for a in host]
         got = (alone.check_soa(dev[0]) if r.kind == "soa" else alone.check_indexed(*dev))
         got = [t.cpu().numpy() for t in got]
         for x, y in zip(r.result, got):
@@ -40,10 +41,10 @@ def test_mix_equals_alone(precision):
         k = min(r.n, 200)
         idx = np.sort(rng.choice(r.n, size=k, replace=False))
         if r.kind == "soa":
-            X = r.arrays[0].numpy()
+            X = host[0].numpy()
             want = oracle.check_soa(np.ascontiguousarray(X[:, :, idx]), max_depth=8)
         else:
-            want = oracle.check_indexed(r.arrays[0].numpy(), r.arrays[1].numpy()[idx], max_depth=8)
+            want = oracle.check_indexed(host[0].numpy(), host[1].numpy()[idx], max_depth=8)
         assert np.array_equal(r.result[0][idx] & 0x7F, want[0] & 0x7F)
     s = serve.latency_summary(reqs)
     print(precision, s)

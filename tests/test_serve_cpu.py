@@ -91,3 +91,39 @@ def test_latency_summary_percentiles():
     s = serve.latency_summary(reqs)
     assert abs(s["p50_ms"] - np.percentile(np.arange(1, 101), 50)) < 1e-9
     assert abs(s["p99_ms"] - np.percentile(np.arange(1, 101), 99)) < 1e-9
+
+
+def test_slot_scratch_is_charged_to_the_budget():
+    """The slots' fixed scratch (here 600 of 1000 bytes) comes off the budget
+    first: a 417-byte request that would fit in the bare budget is refused,
+    a 317-byte one runs."""
+    clk = Clock()
+    ex = FakeExecutor(clk, lambda r: 0.01)
+    ex.fixed_bytes = 600
+    reqs = _reqs([400, 300], [0.0, 0.0])
+    sched = serve.run_stream(reqs, ex, slots=2, budget_bytes=1000, now=clk.now, idle=clk.tick)
+    assert [r.id for r in sched.rejected] == [0]
+    assert reqs[1].done is not None and reqs[0].done is None
+    assert sched.budget == 400
+
+
+def test_latency_by_size_decade():
+    reqs = [serve.Request(i, "soa", (FakeArray(1),), n, 0.0)
+            for i, n in enumerate([150, 900, 5_000, 50_000, 2_000_000, 9_999_999])]
+    for k, r in enumerate(reqs):
+        r.done = 1e-3 * (k + 1)
+    s = serve.latency_summary(reqs)
+    assert list(s["by_size"]) == ["1e2-1e3", "1e3-1e4", "1e4-1e5", "1e6-1e7"]
+    assert s["by_size"]["1e2-1e3"]["requests"] == 2
+    assert abs(s["by_size"]["1e6-1e7"]["p50_ms"] - 5.5) < 1e-9
+
+
+def test_pool_requests_are_cut_lazily():
+    """SoA requests of a pool hold (planes, offset) and no host copy; their
+    byte count is the device footprint of inputs and outputs."""
+    import torch
+    X = torch.arange(8 * 3 * 50, dtype=torch.float64).reshape(8, 3, 50)
+    r = serve.Request(0, "soa", None, 7, 0.0, source=(X, 11))
+    assert r.bytes == (192 + 17) * 7
+    got = r.host_arrays()[0]
+    assert got.is_contiguous() and torch.equal(got, X[:, :, 11:18])

@@ -1,8 +1,8 @@
 """Host logic of the autotuner (tune.py) with the timing stubbed out: it
 times every candidate, re-times the three leaders with three times the
 repetitions and keeps the fastest, tries the double-float redo on the FP32
-winner only, and caches the choice per device, precision, input kind and
-size bucket."""
+winner only, then the placement knobs one at a time, and caches the choice
+per device, precision, input kind and size bucket."""
 import json
 
 import pytest
@@ -19,7 +19,9 @@ def stub(monkeypatch):
     def fake_time(cfg, precision, kind, dev_inputs, reps=20, **caps):
         calls.append((dict(cfg), reps))
         key = (cfg["options"], cfg["bulk_threads"])
-        return speed.get(key, 1.0) + (0.0 if reps == 20 else 0.001)
+        knob = sum(speed.get((k, cfg[k]), 0.0) for k in ("esc_in_pass", "refine_in_pass",
+                                                          "tail_warp_items") if k in cfg)
+        return speed.get(key, 1.0) + knob + (0.0 if reps == 20 else 0.001)
 
     monkeypatch.setattr(tune, "time_config", fake_time)
     monkeypatch.setattr(tune, "_key", lambda p, k, n: "dev|%s|%s|%d" % (p, k, n))
@@ -31,11 +33,14 @@ def test_fastest_leader_is_kept_and_cached(stub, tmp_path):
     speed.update({(0, 64): 0.50, (hv.OPT_PREFETCH, 128): 0.40, (0, 256): 0.45})
     cache = str(tmp_path / "t.json")
     best = tune.best_config("fp32", "indexed", 1000, None, cache=cache, reps=20)
-    assert best == {"options": hv.OPT_PREFETCH, "bulk_threads": 128}
+    defaults = dict(esc_in_pass=4096, refine_in_pass=512, tail_warp_items=8)
+    assert best == dict(options=hv.OPT_PREFETCH, bulk_threads=128, **defaults)
     n_cand = len(tune.candidates("fp32"))
-    assert len(calls) == n_cand + 3 + 1  # all, the three leaders again, the redo trial
-    assert [r for _, r in calls[n_cand:]] == [60, 60, 60, 60]
-    assert calls[-1][0] == {"options": hv.OPT_PREFETCH | hv.OPT_DFREDO, "bulk_threads": 128}
+    n_knob = sum(len(v) - 1 for _, v in tune.KNOBS["fp32"])
+    # all, the three leaders again, the redo trial, the knob trials
+    assert len(calls) == n_cand + 3 + 1 + n_knob
+    assert all(r == 60 for _, r in calls[n_cand:])
+    assert calls[n_cand + 3][0] == {"options": hv.OPT_PREFETCH | hv.OPT_DFREDO, "bulk_threads": 128}
     data = json.load(open(cache))
     assert data["dev|fp32|indexed|1000"]["config"] == best
     calls.clear()
@@ -47,11 +52,26 @@ def test_redo_kept_when_faster_and_never_for_fp64(stub, tmp_path):
     calls, speed = stub
     speed.update({(0, 64): 0.30, (hv.OPT_DFREDO, 64): 0.20})
     best = tune.best_config("fp32", "soa", 10, None, cache=str(tmp_path / "a.json"))
-    assert best == {"options": hv.OPT_DFREDO, "bulk_threads": 64}
+    assert best["options"] == hv.OPT_DFREDO and best["bulk_threads"] == 64
     calls.clear()
     best64 = tune.best_config("fp64", "soa", 10, None, cache=str(tmp_path / "b.json"))
     assert all(not (c["options"] & hv.OPT_DFREDO) for c, _ in calls)
     assert best64["options"] == 0
+
+
+def test_placement_knobs_one_at_a_time(stub, tmp_path):
+    """A knob value is kept when it is faster, and the search goes on from
+    it; the FP64 form tries only the tail threshold."""
+    calls, speed = stub
+    speed.update({(0, 64): 0.30, ("esc_in_pass", 0): -0.05, ("tail_warp_items", 32): -0.02,
+                  ("refine_in_pass", 4096): +0.1})
+    best = tune.best_config("fp32", "indexed", 10, None, cache=str(tmp_path / "k.json"))
+    assert (best["esc_in_pass"], best["refine_in_pass"], best["tail_warp_items"]) == (0, 512, 32)
+    assert [c for c, _ in calls if c.get("tail_warp_items") == 32][0]["esc_in_pass"] == 0
+    calls.clear()
+    best64 = tune.best_config("fp64", "soa", 10, None, cache=str(tmp_path / "k64.json"))
+    assert best64["tail_warp_items"] == 32 and "esc_in_pass" not in best64
+    assert {c.get("tail_warp_items") for c, _ in calls} >= {2, 32}
 
 
 def test_candidates_cover_the_launch_space():
