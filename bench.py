@@ -39,18 +39,41 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 PROFILE_EVERY = 10
+# Roofline denominators of the arithmetic-bound kernels, from the profiling
+# recipe's nominal figures for one GB300 (152 SMs, 2070 MHz): dense FP64 at
+# 1.25 TFLOP/s is 0.625 T FP64 instructions/s (an FMA counts as 2 flops);
+# FP32 at 128 lanes per SM is 40.3 T FP32 instructions/s.
+FP64_PEAK = 1.25 / 2
+FP32_PEAK = 152 * 128 * 2.07e9 / 1e12
+# FP64 instructions of one hexahedron in the FP64 bulk pass: 36 edge
+# components, 36 sums of parallel edges, 20 triple products of 9, and 93 for
+# Table t:Tsmall with its scalings; and of one box expansion (three de
+# Casteljau passes over 9, 15 and 25 rows, 6 operations a row), the same
+# count in FP32 for an FP32 box
+OPS_PER_HEX = 345
+OPS_PER_BOX = 294
 
 
 # ------------------------------------------------------------- workloads ----
 
-def workload(cfg, rank):
-    """Host arrays of one configuration (rank-dependent seed for replicas)."""
-    from paper_1706_01613_gb300 import synth
+def workload(cfg, rank, world=1):
+    """Host arrays of one configuration.  With several ranks the headline
+    mesh is one 128 x 128 x 128N mesh of which each rank takes its element
+    range (a slab of 128^3 hexes with its nodes: weak scaling, no exchange);
+    the other configurations are drawn per rank (rank-dependent seed)."""
+    from paper_1706_01613_gb300 import shard, synth
     if cfg == 2:
-        nodes, conn = synth.structured_grid(128, seed=20170002 + 1000 * rank)
+        name = "structured mesh 128^3 hexes (129^3 FP64 nodes, sigma 0.15, int32 conn)"
+        if world > 1:
+            nodes, conn = synth.structured_grid(128, 128, 128 * world, seed=20170002)
+            nodes, conn, _, _ = shard.shard_indexed(nodes, conn, rank, world)
+            name = ("element range %d of %d of a 128 x 128 x %d structured mesh: 128^3 hexes, "
+                    "%d FP64 nodes (sigma 0.15, int32 conn)" % (rank, world, 128 * world,
+                                                               nodes.shape[0]))
+        else:
+            nodes, conn = synth.structured_grid(128, seed=20170002)
         return dict(kind="indexed", nodes=nodes, conn=conn, n=conn.shape[0], depth=8,
-                    name="structured mesh 128^3 hexes (129^3 FP64 nodes, sigma 0.15, int32 conn)",
-                    bytes_per_hex=32 + 17, n_nodes=nodes.shape[0])
+                    name=name, bytes_per_hex=32 + 17, n_nodes=nodes.shape[0])
     if cfg == 1:
         X = synth.perturbed_cubes(10_000, seed=20170001 + 1000 * rank)
         return dict(kind="soa", X=X, n=X.shape[2], depth=8,
@@ -77,13 +100,14 @@ def workload(cfg, rank):
 
 
 def algorithmic_bytes(w, kernel):
-    """Bytes a launch of `kernel` must move: bulk32 reads the connectivity
-    (32 B/hex) or the 24 FP64 coordinates (192 B/hex), writes 17 B/hex
-    (flag, bmin, bmax), and in the indexed form reads each 16-byte FP32 node
-    record once; nodes32 reads 24 B and writes 16 B per node."""
+    """Bytes the method must move per launch (the per-element figures of the
+    scope table): an element's connectivity (32 B) or its 24 FP64
+    coordinates (192 B), its outputs (17 B: flag, bmin, bmax) and, for an
+    indexed mesh, each FP64 node once (24 B).  nodes32 alone: 24 B read and
+    16 B written per node."""
     if kernel == "nodes32":
         return 40 * w["n_nodes"]
-    return w["bytes_per_hex"] * w["n"] + 16 * w["n_nodes"]
+    return w["bytes_per_hex"] * w["n"] + 24 * w["n_nodes"]
 
 
 # ------------------------------------------------------------ clock probe ---
@@ -193,29 +217,30 @@ def timed_steps(v, w, dev_in, steps, warmup, flush, profile=False):
     return ms, prof, (wall0, wall1), out
 
 
-def e2e_steps(v, w, steps, warmup):
-    """Public API on host data: pinned host inputs copied in, flags copied
-    out, every step."""
+def e2e_steps(v, w, steps, warmup, chunks=4):
+    """Public API on host data: pinned host inputs copied in and all three
+    outputs (flags, bmin, bmax) copied out every step, the copies of each
+    chunk of elements overlapping the checks of the others."""
     import torch
     if w["kind"] == "indexed":
         host = (torch.from_numpy(w["nodes"]).pin_memory(), torch.from_numpy(w["conn"]).pin_memory())
     else:
         host = (torch.from_numpy(w["X"]).pin_memory(),)
     h2d = sum(t.numel() * t.element_size() for t in host)
-    d2h = w["n"]
+    d2h = 17 * w["n"]
     for _ in range(warmup):
-        v.check_host(w["kind"], *host)
+        v.check_host(w["kind"], *host, chunks=chunks)
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record()
     for _ in range(steps):
-        flags = v.check_host(w["kind"], *host)
+        res = v.check_host(w["kind"], *host, chunks=chunks)
     t1.record()
     torch.cuda.synchronize()
     v.raise_on_status()
     ms = t0.elapsed_time(t1) / steps
-    return ms, h2d, d2h, flags
+    return ms, h2d, d2h, res
 
 
 def traffic_for(kernel):
@@ -438,8 +463,9 @@ def serving_run(precision, rate, n_requests, pool, slots=4, budget=40 << 30, see
     from paper_1706_01613_gb300 import serve
     reqs = serve.poisson_stream(pool, n_requests, rate, seed=seed + int(rate),
                                 size_max=pool.max_n)
-    ex = serve.GpuExecutor(slots, precision=precision, max_depth=8, queue_capacity=1 << 21,
-                           max_batch=1 << 24, max_nodes=1 << 24, exact_capacity=1 << 14)
+    ex = serve.GpuExecutor(slots, precision=precision, max_depth=8, keep_results=False,
+                           queue_capacity=1 << 21, max_batch=1 << 24, max_nodes=1 << 24,
+                           exact_capacity=1 << 14)
     try:
         sched = serve.run_stream(reqs, ex, slots=slots, budget_bytes=budget)
         bad = [s for s in ex.status() if s != 0]
@@ -465,6 +491,107 @@ def _oracle_call(w, threads):
     return oracle.check_soa(w["X"], max_depth=w["depth"], threads=threads)
 
 
+# ------------------------------------------------- rooflines, summaries ----
+
+def coeff_err(out32, out64):
+    """bmin/bmax of the FP32-filtered form against the FP64 form's on the
+    same input, relative to the element's largest |bmin|, |bmax|: max and
+    99th percentile over the finite elements."""
+    import torch
+    lo32, hi32, lo64, hi64 = out32[1], out32[2], out64[1], out64[2]
+    fin = torch.isfinite(lo64)
+    scale = torch.maximum(lo64.abs(), hi64.abs())[fin]
+    err = torch.maximum((lo32 - lo64).abs(), (hi32 - hi64).abs())[fin]
+    rel = (err / torch.where(scale > 0, scale, torch.ones_like(scale))).sort().values
+    if rel.numel() == 0:
+        return None
+    return {"max": float(rel[-1]), "p99": float(rel[int(0.99 * (rel.numel() - 1))]),
+            "against": "FP64 form, same input", "elements": int(rel.numel())}
+
+
+def roofline_of(w, prof, stats, calls):
+    """Roofline of the dominant kernel of a form's step, from the per-phase
+    event times: bytes for the bulk passes and the node conversion (HBM),
+    FP64 instructions for the FP64 bulk pass, box expansions for the tail
+    (FP64 boxes on the FP64 pipe, FP32 boxes on the FP32 pipe: the larger
+    fraction is the bound).  Also the phase shares."""
+    phases = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(phases, key=lambda k: phases[k][0])
+    dom_ms = phases[dom][0] / phases[dom][1]
+    share = {k: round(v[0] / sum(x[0] for x in phases.values()), 4) for k, v in phases.items()}
+    hbm, peak_kind = peaks()
+    if dom in ("bulk32", "nodes32"):
+        abytes = algorithmic_bytes(w, dom)
+        achieved = abytes / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind + " (hbm_gbs)",
+                "traffic": traffic_for("bulk32_indexed" if w["kind"] == "indexed"
+                                       else "bulk32_soa") if dom == "bulk32" else None,
+                "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": dom_ms}
+    elif dom == "bulk64":
+        achieved = OPS_PER_HEX * w["n"] / (dom_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "pipe": "fp64", "kernel": dom, "achieved": achieved,
+                "peak": FP64_PEAK,
+                "unit": "T FP64-inst/s", "frac": achieved / FP64_PEAK,
+                "peak_kind": "nominal (1.25 TFLOP/s FP64, FMA = 2 flops)",
+                "ops_per_hex": OPS_PER_HEX, "avg_launch_ms": dom_ms}
+    else:
+        b32 = stats.get("boxes_fp32", 0) / calls
+        b64 = stats.get("boxes", 0) / calls - b32
+        if b32 + b64 == 0:  # nothing to refine: the tail is its launch and barriers
+            return {"bound": "latency", "kernel": dom, "avg_launch_ms": dom_ms,
+                    "note": "no box to split; launch latency dominates"}, share
+        r64 = OPS_PER_BOX * b64 / (dom_ms / 1e3) / 1e12
+        r32 = OPS_PER_BOX * b32 / (dom_ms / 1e3) / 1e12
+        f64, f32 = r64 / FP64_PEAK, r32 / FP32_PEAK
+        roof = {"bound": "alu", "pipe": "fp64" if f64 >= f32 else "fp32", "kernel": dom,
+                "achieved": r64 if f64 >= f32 else r32,
+                "peak": FP64_PEAK if f64 >= f32 else FP32_PEAK,
+                "unit": "T FP64-inst/s" if f64 >= f32 else "T FP32-inst/s",
+                "frac": max(f64, f32), "fp64_frac": f64, "fp32_frac": f32,
+                "peak_kind": "nominal (recipe's unit counts at 2070 MHz)",
+                "box_expansions_per_call": {"fp64": b64, "fp32": b32},
+                "ops_per_box": OPS_PER_BOX, "avg_launch_ms": dom_ms}
+    return roof, share
+
+
+def config_summary(cfg, steps, warmup, flush, retune=False):
+    """One configuration in both forms (tuned launch configurations, device-
+    resident inputs, L2 flushed between steps): throughput, the dominant
+    kernel's roofline, flags equality and the FP32 coefficient error."""
+    import torch
+    from paper_1706_01613_gb300 import hexval as hv
+    from paper_1706_01613_gb300 import tune
+    w = workload(cfg, 0)
+    if w["kind"] == "indexed":
+        dev_in = (torch.from_numpy(w["nodes"]).cuda(), torch.from_numpy(w["conn"]).cuda())
+    else:
+        dev_in = (torch.from_numpy(w["X"]).cuda(),)
+    caps = w.get("caps", {})
+    out = {"workload": w["name"], "n_hex": w["n"], "unit": UNIT}
+    res = {}
+    for prec in ("fp32", "fp64"):
+        k = steps if prec == "fp32" else max(3, steps // 5)
+        cfgp = tune.best_config(prec, w["kind"], w["n"], dev_in, retune=retune,
+                                max_depth=w["depth"], **caps)
+        v = hv.Validator(precision=prec, max_depth=w["depth"], **cfgp, **caps)
+        v.stats(reset=True)
+        ms, prof, _, o = timed_steps(v, w, dev_in, k, warmup, flush, profile=True)
+        st = v.stats()
+        roof, share = roofline_of(w, prof, st, k + warmup)
+        res[prec] = o
+        out[prec] = {"value": w["n"] / (sum(ms) / k / 1e3), "ms_per_step": sum(ms) / k,
+                     "steps": k, "launch": cfgp, "roofline": roof, "phase_share": share,
+                     "stats_per_call": {a: b / (k + warmup) for a, b in st.items()}}
+        v.close()
+    out["value"] = out["fp32"]["value"]
+    out["flags_equal"] = bool(torch.equal(res["fp32"][0] & 0x7F, res["fp64"][0] & 0x7F))
+    out["fp32_coeff_err"] = coeff_err(res["fp32"], res["fp64"])
+    del dev_in, res
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------- main ---
 
 def main():
@@ -480,7 +607,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--serve", action="store_true",
                     help="sweep Poisson arrival rates of the serving workload instead")
-    ap.add_argument("--serve-max-n", type=int, default=1_000_000)
+    ap.add_argument("--serve-max-n", type=int, default=10_000_000)
+    ap.add_argument("--serve-requests", type=int, default=10_000,
+                    help="requests of the serving stream measured in the default run")
+    ap.add_argument("--serve-rate", type=float, default=1000.0,
+                    help="Poisson arrival rate (requests/s) of that stream")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the other configurations and the serving stream")
     ap.add_argument("--retune", action="store_true",
                     help="time every launch configuration again instead of using the cache")
     ap.add_argument("--bulk-threads", type=int, default=None,
@@ -523,7 +656,7 @@ def main():
             print(json.dumps({"metric": METRIC, "mode": "serving sweep",
                               "sizes": [100, args.serve_max_n], "sweep": sweep}))
         return 0
-    w = workload(args.config, rank)
+    w = workload(args.config, rank, world)
     if w["kind"] == "indexed":
         dev_in = (torch.from_numpy(w["nodes"]).cuda(), torch.from_numpy(w["conn"]).cuda())
     else:
@@ -537,11 +670,14 @@ def main():
     from paper_1706_01613_gb300 import tune
     if args.bulk_threads is not None:  # fixed launch configuration (profiling runs)
         tuned = {"options": args.options, "bulk_threads": args.bulk_threads}
+        tuned64 = {}
     else:
         tuned = tune.best_config("fp32", w["kind"], w["n"], dev_in, retune=args.retune,
                                  max_depth=w["depth"], **w.get("caps", {}))
+        tuned64 = tune.best_config("fp64", w["kind"], w["n"], dev_in, retune=args.retune,
+                                   max_depth=w["depth"], **w.get("caps", {}))
     v32 = hv.Validator(precision="fp32", max_depth=w["depth"], **tuned, **w.get("caps", {}))
-    v64 = hv.Validator(precision="fp64", max_depth=w["depth"], **w.get("caps", {}))
+    v64 = hv.Validator(precision="fp64", max_depth=w["depth"], **tuned64, **w.get("caps", {}))
 
     clocks = ClockSampler(bus)
     if rank == 0:
@@ -562,10 +698,13 @@ def main():
 
     # plain FP64 form, same input, fewer steps (about 70x slower)
     k64 = args.fp64_steps or max(3, args.steps // 50)
-    ms64, prof64, _, out64 = timed_steps(v64, w, dev_in, k64, max(3, args.warmup // 5), flush,
-                                         profile=True)
+    w64 = max(3, args.warmup // 5)
+    v64.stats(reset=True)
+    ms64, prof64, _, out64 = timed_steps(v64, w, dev_in, k64, w64, flush, profile=True)
+    st64 = v64.stats()
     value64, tot64 = aggregate(sum(ms64), w["n"], k64, world, dist, "cuda")
     same = bool(torch.equal(out32[0] & 0x7F, out64[0] & 0x7F))
+    err32 = coeff_err(out32, out64)
 
     # end to end through the public API with host buffers
     e2e_ms, h2d, d2h, _ = e2e_steps(v32, w, args.e2e_steps, 3)
@@ -575,29 +714,13 @@ def main():
         dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel of the FP32-filtered step
-    phases = {k: v for k, v in prof32.items() if v[1] > 0}
-    dom = max(phases, key=lambda k: phases[k][0])
-    dom_ms = phases[dom][0] / phases[dom][1]
-    hbm, peak_kind = peaks()
-    if dom in ("bulk32", "nodes32"):
-        abytes = algorithmic_bytes(w, dom)
-        achieved = abytes / (dom_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind + " (hbm_gbs)",
-                "traffic": traffic_for("bulk32_indexed" if w["kind"] == "indexed" else "bulk32_soa"),
-                "algorithmic_bytes_per_launch": abytes, "avg_launch_ms": dom_ms}
-    else:
-        roof = {"bound": "alu", "kernel": dom, "avg_launch_ms": dom_ms}
-    share = {k: round(v[0] / sum(x[0] for x in phases.values()), 4) for k, v in phases.items()}
-
-    # FP64 form: FP64-pipe roofline (instructions of the FP64 unit per hex)
-    fp64_ops_per_hex = 345  # 36 edges + 36 sums + 20 x 9 triple products + 85 (Table t:Tsmall) + 8
-    p64 = {k: v for k, v in prof64.items() if v[1] > 0}
-    b64 = p64.get("bulk64", (0.0, 1))
-    b64_ms = b64[0] / max(1, b64[1])
-    fp64_rate = fp64_ops_per_hex * w["n"] / (b64_ms / 1e3) / 1e12
-    fp64_peak = 0.50  # T FP64 instructions/s, measured DFMA throughput on this machine's GB300
+    # roofline of the dominant kernel of each form's step
+    roof, share = roofline_of(w, prof32, st32, args.steps + args.warmup)
+    if roof["kernel"] == "bulk32":
+        # the same bytes over the whole step (node conversion and tail included)
+        roof["whole_step_frac"] = roof["algorithmic_bytes_per_launch"] / (ms_step / 1e3) / 1e9 / \
+            roof["peak"]
+    roof64, share64 = roofline_of(w, prof64, st64, k64 + w64)
 
     cpu = None
     if world == 1:
@@ -607,39 +730,56 @@ def main():
         rate, sample = oracle_rate(w, args.cpu_seconds, thr)
         cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample}
 
-    # serving: continuous batching of requests of very different sizes
-    from paper_1706_01613_gb300 import serve
-    pool = serve.Pool(args.serve_max_n)
-    latency = serving_run("fp32", 300, 150, pool)
-
     quads = quad_run(max(5, args.steps // 20), 3, flush) if args.quads else None
     filt = filter_run(max(5, args.steps // 50), 3, flush) if args.quads else None
     mj = minj_run(w, dev_in, 5, 2, flush) if args.quads else None
 
+    # the other configurations (device-resident, both forms) and the serving
+    # stream of the scope table: 10,000 requests, sizes log-uniform in
+    # [100, 10^7], Poisson arrivals, both forms
+    others, latency = {}, None
+    if args.configs and args.config == 2:
+        v32.close()
+        v64.close()
+        del dev_in
+        torch.cuda.empty_cache()
+        for c in (1, 3, 4):
+            others["config%d" % c] = config_summary(c, max(20, args.steps // 100), 3, flush,
+                                                    args.retune)
+        from paper_1706_01613_gb300 import serve
+        pool = serve.Pool(args.serve_max_n)
+        latency = {prec: serving_run(prec, args.serve_rate, args.serve_requests, pool)
+                   for prec in ("fp32", "fp64")}
+        del pool
+
     sampled_steps = (args.steps + PROFILE_EVERY - 1) // PROFILE_EVERY
-    launches_per_step = sum(v[1] for v in phases.values()) / sampled_steps
+    launches_per_step = sum(v[1] for v in prof32.values() if v[1] > 0) / sampled_steps
     rec = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (certified, f64/exact escalation)",
         "data": "synthetic",
         "config": {"workload": w["name"], "n_hex": w["n"], "form": "fp32-filtered",
-                   "max_depth": w["depth"], "launch": tuned, "l2": "flushed between steps (256 MB write)",
-                   "parallelism": "replicas (one mesh per GPU, no collective)"},
+                   "max_depth": w["depth"], "launch": tuned, "launch_fp64": tuned64,
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": ("element-range shards of one mesh, one per GPU, no "
+                                   "collective on the data path" if world > 1 and
+                                   args.config == 2 else
+                                   "replicas (one input per GPU, no collective)")},
         "fp64": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": tot64 / k64,
-                 "flags_equal_fp32_form": same,
-                 "roofline": {"bound": "alu", "kernel": "bulk64", "achieved": fp64_rate,
-                              "peak": fp64_peak, "unit": "T FP64-inst/s",
-                              "frac": fp64_rate / fp64_peak, "ops_per_hex": fp64_ops_per_hex,
-                              "avg_launch_ms": b64_ms}},
+                 "flags_equal_fp32_form": same, "roofline": roof64, "phase_share": share64},
+        "fp32_coeff_err": err32,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                "link_gbs": (h2d + d2h) / (e2e_ms / 1e3) / 1e9,
+                "outputs": "flags, bmin, bmax", "chunks": 4},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "roofline": roof,
         "phase_share": share,
         "stats_fp32": st32,
         "cpu_baseline": cpu,
         "latency": latency,
+        "configs": others,
         "quads": quads,
         "filter": filt,
         "min_jacobian": mj,

@@ -135,11 +135,14 @@ typedef struct {
   uint64_t escalated_fp64;  /* FP32 decisions redone at higher precision
                                (double-float or FP64) */
   uint64_t refined;         /* elements that needed subdivision */
-  uint64_t boxes;           /* boxes examined by the refinement */
+  uint64_t boxes;           /* boxes split by the refinement (root boxes
+                               included; the in-warp refinement of the FP32
+                               pass not counted) */
   uint64_t exact;           /* elements decided by the exact tier */
   uint64_t max_level_boxes; /* largest refinement level (boxes) */
   uint64_t escalated_df;    /* of escalated_fp64: decided in double-float
                                (pairs of FP32 values, about 44 bits) */
+  uint64_t boxes_fp32;      /* of boxes: split by the FP32 refinement */
 } hexval_stats;
 
 /* Fills *cfg with the defaults listed above. */

@@ -572,6 +572,7 @@ int hexval_get_stats(hexval_handle h, hexval_stats* out, int reset, void* stream
   out->exact = s.exact;
   out->max_level_boxes = s.max_level_boxes;
   out->escalated_df = s.escalated_df;
+  out->boxes_fp32 = s.boxes_fp32;
   if (reset && cudaMemset(h->s.stats, 0, sizeof(s)) != cudaSuccess) return HEXVAL_E_CUDA;
   return HEXVAL_OK;
 }

@@ -413,10 +413,11 @@ __device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned in
       c = ldcg(&C->level_count[t]);
       c32 = ldcg(&C->level32_count[t]);
     }
-    unsigned long long boxes = c + c32, mx = c > c32 ? c : c32;
+    unsigned long long boxes = c + c32, b32 = c32, mx = c > c32 ? c : c32;
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) {
       boxes += __shfl_xor_sync(0xffffffffu, boxes, d);
+      b32 += __shfl_xor_sync(0xffffffffu, b32, d);
       const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, d);
       mx = o > mx ? o : mx;
     }
@@ -428,7 +429,10 @@ __device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned in
                                          ldcg(&C->esc2_count) + nr_here);
       atomicAdd(&st->refined, static_cast<unsigned long long>(ldcg(&C->level_count[0])) +
                                   (nr - nr_here) + ldcg(&C->iw_done));
-      atomicAdd(&st->boxes, boxes);
+      // box expansions: the root boxes of the refined elements count too
+      // (FP64 roots in level_count[0], FP32 roots in the refinement list)
+      atomicAdd(&st->boxes, boxes + ldcg(&C->level_count[0]) + (nr - nr_here));
+      atomicAdd(&st->boxes_fp32, b32 + (nr - nr_here));
       atomicAdd(&st->exact, static_cast<unsigned long long>(nx));
       atomicAdd(&st->escalated_df, static_cast<unsigned long long>(ldcg(&C->df_count)));
       atomicMax(&st->max_level_boxes, mx);

@@ -50,7 +50,7 @@ class Config(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("elements", "escalated_fp64", "refined", "boxes", "exact", "max_level_boxes",
-                 "escalated_df")]
+                 "escalated_df", "boxes_fp32")]
 
 
 class Profile(ctypes.Structure):
@@ -352,20 +352,68 @@ class Validator:
         _check(rc, "hexval_min_jacobian_indexed")
         return lo, hi, depth
 
-    def check_host(self, kind, *arrays, stream=None):
-        """End-to-end call on host data: copies the inputs (pinned host
-        tensors) to the device, runs the check and copies the flags back.
-        kind = "soa" (corners) or "indexed" (nodes, conn).  Returns the host
-        flags tensor (uint8)."""
+    def check_host(self, kind, *arrays, chunks=4, stream=None):
+        """End-to-end call on host data: pinned host inputs in, pinned host
+        outputs (flags, bmin, bmax) back.  kind = "soa" (corners) or
+        "indexed" (nodes, conn).  The elements are split into `chunks`
+        consecutive ranges whose copies overlap the work on the others:
+        host-to-device copies on one stream, the checks on `stream` (default:
+        the current stream), device-to-host copies on a third; `stream` waits
+        for the last copy, so an event recorded on it after this call marks
+        the outputs as ready.  An indexed mesh copies all its nodes first
+        (every range may use any node)."""
         import torch
-        dev = [a.to(self.device, non_blocking=True) for a in arrays]
-        n = dev[0].shape[2] if kind == "soa" else dev[1].shape[0]
-        flags = torch.empty(n, dtype=torch.uint8, device=self.device)
-        if kind == "soa":
-            self.check_soa(dev[0], out=(flags, None, None), stream=stream)
-        else:
-            self.check_indexed(dev[0], dev[1], out=(flags, None, None), stream=stream)
-        return flags.to("cpu")
+        dev = self.device
+        main = stream if stream is not None else torch.cuda.current_stream(dev)
+        if not hasattr(self, "_copy_streams"):
+            self._copy_streams = (torch.cuda.Stream(dev), torch.cuda.Stream(dev))
+        cin, cout = self._copy_streams
+        cin.wait_stream(main)
+        n = arrays[0].shape[2] if kind == "soa" else arrays[1].shape[0]
+        host = (torch.empty(n, dtype=torch.uint8, pin_memory=True),
+                torch.empty(n, dtype=torch.float64, pin_memory=True),
+                torch.empty(n, dtype=torch.float64, pin_memory=True))
+        with torch.cuda.stream(main):
+            out = (torch.empty(n, dtype=torch.uint8, device=dev),
+                   torch.empty(n, dtype=torch.float64, device=dev),
+                   torch.empty(n, dtype=torch.float64, device=dev))
+        for t in out:  # read by the device-to-host stream too
+            t.record_stream(cout)
+        k = max(1, min(int(chunks), n))
+        bounds = [n * i // k for i in range(k + 1)]
+        with torch.cuda.stream(cin):
+            if kind == "indexed":
+                nodes = arrays[0].to(dev, non_blocking=True)
+                conn = torch.empty(arrays[1].shape, dtype=arrays[1].dtype, device=dev)
+                nodes.record_stream(main)  # used by the checks on `main`
+                conn.record_stream(main)
+            else:
+                planes = arrays[0].view(24, n)
+        for i in range(k):
+            lo, hi = bounds[i], bounds[i + 1]
+            if hi == lo:
+                continue
+            with torch.cuda.stream(cin):
+                if kind == "indexed":
+                    conn[lo:hi].copy_(arrays[1][lo:hi], non_blocking=True)
+                else:
+                    X = torch.empty((8, 3, hi - lo), dtype=torch.float64, device=dev)
+                    X.record_stream(main)
+                    rows = X.view(24, hi - lo)
+                    for r in range(24):  # each plane's columns are contiguous
+                        rows[r].copy_(planes[r, lo:hi], non_blocking=True)
+            main.wait_stream(cin)
+            o = tuple(t[lo:hi] for t in out)
+            if kind == "indexed":
+                self.check_indexed(nodes, conn[lo:hi], out=o, stream=main)
+            else:
+                self.check_soa(X, out=o, stream=main)
+            cout.wait_stream(main)
+            with torch.cuda.stream(cout):
+                for h, d in zip(host, o):
+                    h[lo:hi].copy_(d, non_blocking=True)
+        main.wait_stream(cout)
+        return host
 
     def scratch_bytes(self):
         """Device bytes held by this handle's scratch."""

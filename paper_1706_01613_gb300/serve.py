@@ -150,10 +150,13 @@ def latency_summary(requests):
 class GpuExecutor:
     """Runs requests through the library, one handle and stream per slot."""
 
-    def __init__(self, slots, precision="fp32", max_depth=8, **caps):
+    def __init__(self, slots, precision="fp32", max_depth=8, keep_results=True, **caps):
         import torch
         from . import hexval as hv
         self.torch = torch
+        # False: a finished request keeps only its verdict counts (a long
+        # stream's outputs would otherwise pile up in host memory)
+        self.keep_results = keep_results
         self.v = [hv.Validator(precision=precision, max_depth=max_depth, **caps)
                   for _ in range(slots)]
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
@@ -208,7 +211,10 @@ class GpuExecutor:
         ev = self.events[slot]
         ev.synchronize()
         _, _, host = self.buffers[slot]
-        req.result = tuple(h.numpy() for h in host)
+        if self.keep_results:
+            req.result = tuple(h.numpy() for h in host)
+        else:
+            req.result = np.bincount(host[0].numpy() & 7, minlength=8)
         self.buffers[slot] = None
         done = self.t0_host + self.t0.elapsed_time(ev) / 1e3
         return done - self.t0_host

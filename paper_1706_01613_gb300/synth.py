@@ -66,26 +66,25 @@ def structured_grid(nx=128, ny=None, nz=None, sigma=0.15, seed=None):
     return nodes, conn
 
 
-def _per_element(fn, *arrays, chunk=1 << 18):
-    """fn applied to consecutive chunks of the leading axis, on the host's
-    cores (the random numbers are drawn beforehand, and fn works element by
-    element, so the result is the same as one call)."""
+def _for_chunks(fn, n, chunk=1 << 18):
+    """fn(slice) over consecutive chunks of range(n) on the host's cores (fn
+    writes its own part of the output; the random numbers are drawn
+    beforehand, so the result does not depend on the chunking)."""
     import concurrent.futures as cf
     import os
-    n = arrays[0].shape[0]
-    if n <= chunk:
-        return fn(*arrays)
     parts = [slice(i, min(n, i + chunk)) for i in range(0, n, chunk)]
+    if len(parts) <= 1:
+        for sl in parts:
+            fn(sl)
+        return
     with cf.ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
-        out = list(ex.map(lambda sl: fn(*(a[sl] for a in arrays)), parts))
-    if isinstance(out[0], tuple):
-        return tuple(np.concatenate([o[k] for o in out]) for k in range(len(out[0])))
-    return np.concatenate(out)
+        list(ex.map(fn, parts))
 
 
-def _random_rotations(rng, n):
-    G = rng.normal(size=(n, 3, 3))
-    Q, R = _per_element(np.linalg.qr, G)
+def _rotations_from(G):
+    """Proper rotations from Gaussian matrices (QR with the diagonal of R made
+    positive, then one column flipped where the determinant is negative)."""
+    Q, R = np.linalg.qr(G)
     d = np.sign(np.diagonal(R, axis1=1, axis2=2))
     d[d == 0] = 1.0
     Q = Q * d[:, None, :]
@@ -107,37 +106,47 @@ def affine_mixture(n, seed=None, frac_degenerate=0.05, frac_inverted=0.05, r_max
     Returns (corners (8,3,n) f64, kind (n,) int8: 0 affine, 1 near-degenerate,
     2 inverted, r (n,) f64 for the near-degenerate ones, else 0)."""
     rng = rng_for(3, seed)
-    R = _random_rotations(rng, n)
-    S = np.tile(np.eye(3), (n, 1, 1))
-    S[:, 0, 1] = rng.uniform(-1, 1, n)
-    S[:, 0, 2] = rng.uniform(-1, 1, n)
-    S[:, 1, 2] = rng.uniform(-1, 1, n)
+    # every random number first, in a fixed order; then the elements chunk by
+    # chunk straight into the output planes (bounded host memory)
+    G = rng.normal(size=(n, 3, 3))
+    shear = [rng.uniform(-1, 1, n) for _ in range(3)]
     log_delta = rng.uniform(math.log(1e-3), math.log(1e3), n)
     u = rng.uniform(-1, 1, size=(n, 3))
-    u -= u.mean(axis=1, keepdims=True)
-    D = np.exp(log_delta[:, None] / 3.0 + u)
-    A = R @ S * D[:, None, :]
     t = rng.uniform(-10, 10, size=(n, 3))
-    ref = np.broadcast_to(REF_CORNERS[None], (n, 8, 3)).copy()
     kind = np.zeros(n, np.int8)
     pick = rng.uniform(size=n)
     kind[pick < frac_degenerate + frac_inverted] = 2
     kind[pick < frac_degenerate] = 1
     corner = rng.integers(0, 8, n)
     r = np.where(kind == 1, rng.uniform(-r_max, r_max, n), 0.0)
+    out = np.empty((8, 3, n))
     centre = np.full(3, 0.5)
-    idx = np.nonzero(kind == 1)[0]
-    s = (1.0 - r[idx]) / 3.0
-    ck = REF_CORNERS[corner[idx]]
-    ref[idx, corner[idx]] = ck + 2.0 * s[:, None] * (centre - ck)
-    idx = np.nonzero(kind == 2)[0]
-    ck = REF_CORNERS[corner[idx]]
-    # the three edge neighbours of corner C_k differ from it in one coordinate;
-    # their plane is sum_d |x_d - C_kd| = 1, and the mirror image of C_k in it
-    # is C_k + (4/3) (centre - C_k)
-    ref[idx, corner[idx]] = ck + (4.0 / 3.0) * (centre - ck)
-    X = _per_element(lambda a, c: np.einsum("nij,nkj->nki", a, c), A, ref) + t[:, None, :]
-    return np.ascontiguousarray(X.transpose(1, 2, 0)), kind, r
+
+    def chunk(sl):
+        m = sl.stop - sl.start
+        R = _rotations_from(G[sl])
+        S = np.tile(np.eye(3), (m, 1, 1))
+        S[:, 0, 1], S[:, 0, 2], S[:, 1, 2] = shear[0][sl], shear[1][sl], shear[2][sl]
+        uc = u[sl] - u[sl].mean(axis=1, keepdims=True)
+        D = np.exp(log_delta[sl, None] / 3.0 + uc)
+        A = R @ S * D[:, None, :]
+        ref = np.broadcast_to(REF_CORNERS[None], (m, 8, 3)).copy()
+        kc, cc, rc = kind[sl], corner[sl], r[sl]
+        idx = np.nonzero(kc == 1)[0]
+        s_ = (1.0 - rc[idx]) / 3.0
+        ck = REF_CORNERS[cc[idx]]
+        ref[idx, cc[idx]] = ck + 2.0 * s_[:, None] * (centre - ck)
+        idx = np.nonzero(kc == 2)[0]
+        ck = REF_CORNERS[cc[idx]]
+        # the three edge neighbours of corner C_k differ from it in one
+        # coordinate; their plane is sum_d |x_d - C_kd| = 1, and the mirror
+        # image of C_k in it is C_k + (4/3) (centre - C_k)
+        ref[idx, cc[idx]] = ck + (4.0 / 3.0) * (centre - ck)
+        X = np.einsum("nij,nkj->nki", A, ref) + t[sl, None, :]
+        out[:, :, sl] = X.transpose(1, 2, 0)
+
+    _for_chunks(chunk, n)
+    return out, kind, r
 
 
 def twisted_layers(n, seed=None, theta_max_deg=120.0, ar_max=1e3, noise=0.01):

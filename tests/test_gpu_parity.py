@@ -629,3 +629,29 @@ def test_placement_knobs_do_not_change_results(kind):
     base = {"fp32": runs[0][1], "fp64": runs[1][1]}
     for prec, got in runs[2:]:
         assert np.array_equal(got[0] & 0x7F, base[prec][0] & 0x7F)
+
+
+@pytest.mark.parametrize("kind,chunks", [("indexed", 1), ("indexed", 4), ("soa", 3)])
+def test_host_buffers_pipeline(kind, chunks):
+    """The end-to-end call on pinned host buffers (inputs copied in chunk by
+    chunk while earlier chunks are checked, all three outputs copied back)
+    gives the device-resident call's flags and the oracle's, with bounds
+    within each element's certified bound."""
+    v = hv.Validator(precision="fp32", max_depth=8, **CAPS)
+    if kind == "indexed":
+        nodes, conn = synth.structured_grid(30, 21, 17, sigma=0.3, seed=95)
+        host = (torch.from_numpy(nodes).pin_memory(), torch.from_numpy(conn).pin_memory())
+        want = [t.cpu().numpy() for t in v.check_indexed(host[0].cuda(), host[1].cuda())]
+        oracle_out, X = oracle.check_indexed(nodes, conn, max_depth=8), _soa(nodes, conn)
+    else:
+        X = synth.perturbed_cubes(10_007, noise=0.45, seed=96)
+        host = (torch.from_numpy(X).pin_memory(),)
+        want = [t.cpu().numpy() for t in v.check_soa(host[0].cuda())]
+        oracle_out = oracle.check_soa(X, max_depth=8)
+    got = v.check_host(kind, *host, chunks=chunks)
+    torch.cuda.synchronize()
+    got = [t.numpy() for t in got]
+    assert np.array_equal(got[0] & 0x7F, want[0] & 0x7F)
+    _compare("fp32", got, oracle_out, X)
+    assert v.status() == 0
+    v.close()
