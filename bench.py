@@ -45,22 +45,24 @@ PROFILE_EVERY = 10
 # FP32 at 128 lanes per SM is 40.3 T FP32 instructions/s.
 FP64_PEAK = 1.25 / 2
 FP32_PEAK = 152 * 128 * 2.07e9 / 1e12
-# FP64 instructions of one hexahedron in the FP64 bulk pass: 36 edge
-# components, 36 sums of parallel edges, 20 triple products of 9, and 93 for
-# Table t:Tsmall with its scalings; and of one box expansion (three de
-# Casteljau passes over 9, 15 and 25 rows, 6 operations a row), the same
-# count in FP32 for an FP32 box
-OPS_PER_HEX = 345
+# FP64 instructions of one hexahedron in the FP64 bulk pass, as ncu counts
+# them (DADD 132, DFMA 107, DMUL 103 per element on the 128^3 mesh:
+# profiles/bulk64_mesh128.txt), and of one box expansion (three de Casteljau
+# passes over 9, 15 and 25 rows, 6 operations a row; the same count in FP32
+# for an FP32 box)
+OPS_PER_HEX = 366
 OPS_PER_BOX = 294
 
 
 # ------------------------------------------------------------- workloads ----
 
-def workload(cfg, rank, world=1):
+def workload(cfg, rank, world=1, n=None):
     """Host arrays of one configuration.  With several ranks the headline
     mesh is one 128 x 128 x 128N mesh of which each rank takes its element
     range (a slab of 128^3 hexes with its nodes: weak scaling, no exchange);
-    the other configurations are drawn per rank (rank-dependent seed)."""
+    the other configurations are drawn per rank (rank-dependent seed).  n:
+    a smaller case of the same SoA workload (its first n elements), for
+    profiler captures that must stay small."""
     from paper_1706_01613_gb300 import shard, synth
     if cfg == 2:
         name = "structured mesh 128^3 hexes (129^3 FP64 nodes, sigma 0.15, int32 conn)"
@@ -75,27 +77,31 @@ def workload(cfg, rank, world=1):
         return dict(kind="indexed", nodes=nodes, conn=conn, n=conn.shape[0], depth=8,
                     name=name, bytes_per_hex=32 + 17, n_nodes=nodes.shape[0])
     if cfg == 1:
-        X = synth.perturbed_cubes(10_000, seed=20170001 + 1000 * rank)
+        X = synth.perturbed_cubes(n or 10_000, seed=20170001 + 1000 * rank)
         return dict(kind="soa", X=X, n=X.shape[2], depth=8,
-                    name="10,000 perturbed unit cubes (U[-0.3,0.3], SoA FP64)",
+                    name="{:,} perturbed unit cubes (U[-0.3,0.3], SoA FP64)".format(X.shape[2]),
                     bytes_per_hex=192 + 17, n_nodes=0)
     if cfg == 3:
-        X, _, _ = synth.affine_mixture(16_777_216, seed=20170003 + 1000 * rank)
+        X, _, _ = synth.affine_mixture(n or 16_777_216, seed=20170003 + 1000 * rank)
         return dict(kind="soa", X=X, n=X.shape[2], depth=8,
-                    name="16,777,216 affine / near-degenerate / inverted hexes (SoA FP64)",
+                    name="{:,} affine / near-degenerate / inverted hexes (SoA FP64)".format(
+                        X.shape[2]),
                     bytes_per_hex=192 + 17, n_nodes=0)
     if cfg == 4:
-        X = synth.twisted_layers(4_194_304, seed=20170004 + 1000 * rank)
+        X = synth.twisted_layers(n or 4_194_304, seed=20170004 + 1000 * rank)
         return dict(kind="soa", X=X, n=X.shape[2], depth=10,
-                    name="4,194,304 twisted boundary-layer hexes (SoA FP64, depth cap 10)",
+                    name="{:,} twisted boundary-layer hexes (SoA FP64, depth cap 10)".format(
+                        X.shape[2]),
                     bytes_per_hex=192 + 17, n_nodes=0)
     if cfg == "4b":  # stress variant: twists up to 180 degrees, deep refinement
-        X = synth.twisted_layers(4_194_304, seed=20170004 + 1000 * rank, theta_max_deg=180.0)
+        X = synth.twisted_layers(n or 4_194_304, seed=20170004 + 1000 * rank,
+                                 theta_max_deg=180.0)
         return dict(kind="soa", X=X, n=X.shape[2], depth=10,
-                    name="4,194,304 boundary-layer hexes twisted by up to 180 degrees "
-                         "(SoA FP64, depth cap 10)",
+                    name="{:,} boundary-layer hexes twisted by up to 180 degrees (SoA FP64, "
+                         "depth cap 10)".format(X.shape[2]),
                     bytes_per_hex=192 + 17, n_nodes=0,
-                    caps=dict(queue_capacity=1 << 25))  # ~2.6 live boxes per element
+                    caps=dict(queue_capacity=min(1 << 25, 8 * X.shape[2])))  # ~2.6 live boxes
+                                                                          # per element
     raise ValueError(cfg)
 
 
@@ -538,10 +544,11 @@ def roofline_of(w, prof, stats, calls):
     else:
         b32 = stats.get("boxes_fp32", 0) / calls
         b64 = stats.get("boxes", 0) / calls - b32
-        if b32 + b64 == 0:  # nothing to refine: the tail is its launch and barriers
+        redo = stats.get("redone_tail", 0) / calls
+        if b32 + b64 + redo == 0:  # nothing to do: the tail is its launch and barriers
             return {"bound": "latency", "kernel": dom, "avg_launch_ms": dom_ms,
-                    "note": "no box to split; launch latency dominates"}, share
-        r64 = OPS_PER_BOX * b64 / (dom_ms / 1e3) / 1e12
+                    "note": "no box to split, no element to redo; launch latency"}, share
+        r64 = (OPS_PER_BOX * b64 + OPS_PER_HEX * redo) / (dom_ms / 1e3) / 1e12
         r32 = OPS_PER_BOX * b32 / (dom_ms / 1e3) / 1e12
         f64, f32 = r64 / FP64_PEAK, r32 / FP32_PEAK
         roof = {"bound": "alu", "pipe": "fp64" if f64 >= f32 else "fp32", "kernel": dom,
@@ -551,7 +558,8 @@ def roofline_of(w, prof, stats, calls):
                 "frac": max(f64, f32), "fp64_frac": f64, "fp32_frac": f32,
                 "peak_kind": "nominal (recipe's unit counts at 2070 MHz)",
                 "box_expansions_per_call": {"fp64": b64, "fp32": b32},
-                "ops_per_box": OPS_PER_BOX, "avg_launch_ms": dom_ms}
+                "fp64_redone_per_call": redo, "ops_per_box": OPS_PER_BOX,
+                "ops_per_hex": OPS_PER_HEX, "avg_launch_ms": dom_ms}
     return roof, share
 
 
@@ -603,6 +611,8 @@ def main():
     ap.add_argument("--config", type=lambda c: c if c == "4b" else int(c), default=2,
                     choices=[1, 2, 3, 4, "4b"])
     ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--n", type=int, default=None,
+                    help="first n elements of an SoA configuration (small profiler cases)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--serve", action="store_true",
@@ -656,7 +666,7 @@ def main():
             print(json.dumps({"metric": METRIC, "mode": "serving sweep",
                               "sizes": [100, args.serve_max_n], "sweep": sweep}))
         return 0
-    w = workload(args.config, rank, world)
+    w = workload(args.config, rank, world, args.n)
     if w["kind"] == "indexed":
         dev_in = (torch.from_numpy(w["nodes"]).cuda(), torch.from_numpy(w["conn"]).cuda())
     else:

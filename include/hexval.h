@@ -143,6 +143,8 @@ typedef struct {
   uint64_t escalated_df;    /* of escalated_fp64: decided in double-float
                                (pairs of FP32 values, about 44 bits) */
   uint64_t boxes_fp32;      /* of boxes: split by the FP32 refinement */
+  uint64_t redone_tail;     /* elements redone in FP64 by the tail kernel
+                               (escalations the FP32 pass left) */
 } hexval_stats;
 
 /* Fills *cfg with the defaults listed above. */
@@ -157,6 +159,17 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out);
 
 /* Frees the handle's scratch (synchronises its device). */
 int hexval_destroy(hexval_handle h);
+
+/* Copies the elements [first, first + n) of SoA corner planes src (24 planes
+ * of n_src values each, laid out as for hexval_check_soa; host -- pinned for
+ * an asynchronous copy -- or device memory) into dst, 24 planes of n values
+ * (device), with one strided copy on `stream`.  For feeding element ranges
+ * of a large input to hexval_check_soa (a server cutting requests, a caller
+ * overlapping copies with checks) without a host-side gather.  Not from the
+ * paper: data movement of this library.  Stream-ordered, no allocation;
+ * HEXVAL_E_ARG for a range outside [0, n_src). */
+int hexval_copy_soa_range(double* dst, const double* src, int64_t n_src, int64_t first,
+                          int64_t n, void* stream);
 
 /* Device bytes the handle holds (the scratch allocated by hexval_create),
  * for callers that budget device memory, such as a server admitting

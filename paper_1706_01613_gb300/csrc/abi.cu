@@ -537,6 +537,18 @@ int hexval_min_jacobian_indexed(hexval_handle h, int64_t n_nodes, const double* 
              : HEXVAL_E_CUDA;
 }
 
+int hexval_copy_soa_range(double* dst, const double* src, int64_t n_src, int64_t first,
+                          int64_t n, void* stream) {
+  if (!dst || !src || n_src < 0 || first < 0 || n < 0 || first + n > n_src) return HEXVAL_E_ARG;
+  if (n == 0) return HEXVAL_OK;
+  const size_t width = static_cast<size_t>(n) * sizeof(double);
+  return cudaMemcpy2DAsync(dst, width, src + first, static_cast<size_t>(n_src) * sizeof(double),
+                           width, 24, cudaMemcpyDefault,
+                           static_cast<cudaStream_t>(stream)) == cudaSuccess
+             ? HEXVAL_OK
+             : HEXVAL_E_CUDA;
+}
+
 int hexval_scratch_bytes(hexval_handle h, uint64_t* bytes) {
   if (!h || !bytes) return HEXVAL_E_ARG;
   *bytes = h->scratch_bytes;
@@ -573,6 +585,7 @@ int hexval_get_stats(hexval_handle h, hexval_stats* out, int reset, void* stream
   out->max_level_boxes = s.max_level_boxes;
   out->escalated_df = s.escalated_df;
   out->boxes_fp32 = s.boxes_fp32;
+  out->redone_tail = s.redone_tail;
   if (reset && cudaMemset(h->s.stats, 0, sizeof(s)) != cudaSuccess) return HEXVAL_E_CUDA;
   return HEXVAL_OK;
 }

@@ -96,7 +96,7 @@ constexpr unsigned int kIwBoxes = 64;
 // Counters accumulated across calls (hexval_get_stats).
 struct Stats {
   unsigned long long elements, escalated_fp64, refined, boxes, exact, max_level_boxes,
-      escalated_df, boxes_fp32;
+      escalated_df, boxes_fp32, redone_tail;
 };
 
 // Device scratch owned by a handle.

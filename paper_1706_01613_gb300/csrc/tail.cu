@@ -402,7 +402,8 @@ __device__ __forceinline__ bool tail_barrier(unsigned int* arrive, unsigned int&
 // of one block, once every block of the batch's last kernel is done with the
 // counters.  Warp 0 reads them (the per-level counts one per lane), then the
 // block zeroes them together.
-__device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned int nx) {
+__device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned int nx,
+                                                     unsigned int n_redo) {
   const Scratch& S = p.s;
   Counters* C = S.cnt;
   Stats* st = S.stats;
@@ -436,6 +437,7 @@ __device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned in
       atomicAdd(&st->exact, static_cast<unsigned long long>(nx));
       atomicAdd(&st->escalated_df, static_cast<unsigned long long>(ldcg(&C->df_count)));
       atomicMax(&st->max_level_boxes, mx);
+      atomicAdd(&st->redone_tail, static_cast<unsigned long long>(n_redo));
     }
   }
   __syncthreads();  // every read above is done before the reset
@@ -461,7 +463,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
   if (n_esc == 0 && n_r == 0 && ldcg(&C->level_count[0]) == 0 && ldcg(&C->exact_count) == 0) {
     // nothing left: every block reads only counters that are, or become,
     // zero here, so block 0 may end the batch at once
-    if (blockIdx.x == 0) fold_stats_and_reset(p, 0u);
+    if (blockIdx.x == 0) fold_stats_and_reset(p, 0u, 0u);
     return;
   }
   __shared__ double wsm[kTailThreads / 32][kWarpScratch];
@@ -471,6 +473,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
   const unsigned int warp_items = p.warp_items * gridDim.x * (blockDim.x >> 5);
   unsigned int epoch = 0;
   unsigned int n_esc2 = 0;
+  unsigned int n_redo = 0;  // elements of phase E
   // false once a grid barrier timed out: the block then skips to the end
   bool go = true;
   auto sync = [&]() {
@@ -496,6 +499,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
   if (go && n_esc + n_esc2) {  // phase E: list entries, then the FP32 refinement's
     const uint32_t* esc = p.dfredo ? S.esc3 : S.esc + p.esc_in_pass;
     const unsigned int n_e = n_esc + n_esc2;
+    n_redo = n_e;
     if (n_e <= warp_items) {
       FOR_EACH_WARP_ITEM(n_e, i)
         fp64_element_warp(p, i < n_esc ? ldcg(esc + i) : ldcg(S.esc2 + (i - n_esc)), mysm);
@@ -571,7 +575,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
   __syncthreads();
   if (last_block) {
     __threadfence();
-    fold_stats_and_reset(p, nx);
+    fold_stats_and_reset(p, nx, n_redo);
   }
 }
 

@@ -32,7 +32,8 @@ EXPORTS = ("hexval_config_default", "hexval_create", "hexval_destroy", "hexval_c
            "hexval_profile_read", "hexval_check_soa_noalloc", "hexval_check_quads",
            "hexval_check_quads_indexed", "hexval_corner_quality",
            "hexval_corner_quality_indexed", "hexval_compact", "hexval_min_jacobian",
-           "hexval_min_jacobian_indexed", "hexval_strerror", "hexval_scratch_bytes")
+           "hexval_min_jacobian_indexed", "hexval_strerror", "hexval_scratch_bytes",
+           "hexval_copy_soa_range")
 PHASES = ("nodes32", "bulk32", "bulk64", "tail", "-", "redo_df", "-", "-")
 
 
@@ -50,7 +51,7 @@ class Config(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("elements", "escalated_fp64", "refined", "boxes", "exact", "max_level_boxes",
-                 "escalated_df", "boxes_fp32")]
+                 "escalated_df", "boxes_fp32", "redone_tail")]
 
 
 class Profile(ctypes.Structure):
@@ -91,6 +92,7 @@ def load(build_if_missing=False):
     lib.hexval_check_indexed.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, vp]
     lib.hexval_status.argtypes = [vp, vp]
     lib.hexval_scratch_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.hexval_copy_soa_range.argtypes = [vp, vp, i64, i64, i64, vp]
     lib.hexval_get_stats.argtypes = [vp, ctypes.POINTER(Stats), ctypes.c_int, vp]
     lib.hexval_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.hexval_profile_read.argtypes = [vp, ctypes.POINTER(Profile), ctypes.c_int]
@@ -387,8 +389,6 @@ class Validator:
                 conn = torch.empty(arrays[1].shape, dtype=arrays[1].dtype, device=dev)
                 nodes.record_stream(main)  # used by the checks on `main`
                 conn.record_stream(main)
-            else:
-                planes = arrays[0].view(24, n)
         for i in range(k):
             lo, hi = bounds[i], bounds[i + 1]
             if hi == lo:
@@ -399,9 +399,7 @@ class Validator:
                 else:
                     X = torch.empty((8, 3, hi - lo), dtype=torch.float64, device=dev)
                     X.record_stream(main)
-                    rows = X.view(24, hi - lo)
-                    for r in range(24):  # each plane's columns are contiguous
-                        rows[r].copy_(planes[r, lo:hi], non_blocking=True)
+                    copy_soa_range(X, arrays[0], lo, stream=cin)
             main.wait_stream(cin)
             o = tuple(t[lo:hi] for t in out)
             if kind == "indexed":
@@ -446,6 +444,21 @@ class Validator:
         _check(self._lib.hexval_get_stats(self._h, ctypes.byref(s), int(reset),
                                           _stream_ptr(stream)), "hexval_get_stats")
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+def copy_soa_range(dst, src, first, stream=None):
+    """dst (8, 3, n) CUDA tensor <- the elements [first, first + n) of the SoA
+    planes src (8, 3, N), host (pinned) or device, in one strided copy on
+    `stream` (default: the current stream)."""
+    n, N = dst.shape[2], src.shape[2]
+    if (dst.dtype != src.dtype or not dst.is_cuda or not dst.is_contiguous()
+            or not src.is_contiguous() or tuple(src.shape[:2]) != (8, 3)):
+        raise ValueError("dst: contiguous CUDA (8, 3, n); src: contiguous (8, 3, N), same dtype")
+    rc = load().hexval_copy_soa_range(ctypes.c_void_p(dst.data_ptr()),
+                                      ctypes.c_void_p(src.data_ptr()), N, int(first), n,
+                                      _stream_ptr(stream))
+    _check(rc, "hexval_copy_soa_range")
+    return dst
 
 
 NOALLOC_MAX_HEX = 16384

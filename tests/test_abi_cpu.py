@@ -114,3 +114,14 @@ def test_options_outside_the_known_bits_are_refused(lib):
 def test_placement_defaults():
     cfg = hv.default_config()
     assert (cfg.esc_in_pass, cfg.refine_in_pass, cfg.tail_warp_items) == (4096, 512, 8)
+
+
+def test_copy_soa_range_refuses_bad_ranges(lib):
+    """The range copy checks its range on the host and enqueues nothing on
+    error (no device needed to see the refusal)."""
+    buf = ctypes.create_string_buffer(24 * 8 * 10)
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert lib.hexval_copy_soa_range(None, p, 10, 0, 5, None) == -1
+    assert lib.hexval_copy_soa_range(p, p, 10, 6, 5, None) == -1
+    assert lib.hexval_copy_soa_range(p, p, 10, -1, 5, None) == -1
+    assert lib.hexval_copy_soa_range(p, p, 10, 3, 0, None) == 0  # empty: nothing to do

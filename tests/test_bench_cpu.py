@@ -52,7 +52,7 @@ def test_roofline_of_each_dominant_kernel(bench):
     assert abs(roof["achieved"] - 209 * 10_000 / 0.2e-3 / 1e9) < 1e-9
     assert abs(sum(share.values()) - 1) < 1e-3
     roof, _ = bench.roofline_of(w, {"bulk64": (3.0, 3)}, {}, 3)
-    assert roof["pipe"] == "fp64" and abs(roof["frac"] - 345 * 10_000 / 1e-3 / 1e12 / 0.625) < 1e-9
+    assert roof["pipe"] == "fp64" and abs(roof["frac"] - 366 * 10_000 / 1e-3 / 1e12 / 0.625) < 1e-9
     stats = {"boxes": 3_000_000, "boxes_fp32": 1_000_000}
     roof, _ = bench.roofline_of(w, {"bulk32": (0.1, 1), "tail": (20.0, 10)}, stats, 10)
     assert roof["kernel"] == "tail" and roof["pipe"] == "fp64"
@@ -60,3 +60,6 @@ def test_roofline_of_each_dominant_kernel(bench):
     assert abs(roof["fp64_frac"] - 294 * 200_000 / 2e-3 / 1e12 / 0.625) < 1e-9
     roof, _ = bench.roofline_of(w, {"bulk32": (0.1, 1), "tail": (2.0, 10)}, {}, 10)
     assert roof["bound"] == "latency"
+    roof, _ = bench.roofline_of(w, {"bulk32": (0.1, 1), "tail": (2.0, 10)},
+                                {"redone_tail": 1_000_000}, 10)
+    assert roof["pipe"] == "fp64" and abs(roof["frac"] - 366 * 100_000 / 0.2e-3 / 1e12 / 0.625) < 1e-9

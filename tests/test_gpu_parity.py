@@ -655,3 +655,16 @@ def test_host_buffers_pipeline(kind, chunks):
     _compare("fp32", got, oracle_out, X)
     assert v.status() == 0
     v.close()
+
+
+def test_copy_soa_range_from_host_and_device():
+    """One strided copy of an element range of SoA planes, from pinned host
+    memory and from device memory, equals the slice."""
+    X = torch.from_numpy(synth.perturbed_cubes(5000, seed=97)).pin_memory()
+    for src in (X, X.cuda()):
+        dst = torch.empty((8, 3, 1234), dtype=torch.float64, device="cuda")
+        hv.copy_soa_range(dst, src, 2345)
+        torch.cuda.synchronize()
+        assert torch.equal(dst.cpu(), X[:, :, 2345:2345 + 1234])
+    with pytest.raises(hv.HexvalError):
+        hv.copy_soa_range(torch.empty((8, 3, 10), dtype=torch.float64, device="cuda"), X, 4995)
