@@ -620,7 +620,7 @@ def main():
     ap.add_argument("--serve-max-n", type=int, default=10_000_000)
     ap.add_argument("--serve-requests", type=int, default=10_000,
                     help="requests of the serving stream measured in the default run")
-    ap.add_argument("--serve-rate", type=float, default=1000.0,
+    ap.add_argument("--serve-rate", type=float, default=300.0,
                     help="Poisson arrival rate (requests/s) of that stream")
     ap.add_argument("--no-configs", dest="configs", action="store_false",
                     help="skip the other configurations and the serving stream")

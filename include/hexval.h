@@ -111,6 +111,15 @@ typedef struct {
  *                      asynchronous copies: connectivity two tiles ahead,
  *                      node records one tile ahead (ignored with
  *                      HEXVAL_OPT_PAIR32);
+ *  HEXVAL_OPT_LEVEL1   FP32 form: the elements listed for the FP32
+ *                      refinement get their first refinement level (split
+ *                      of the root box, classification of the 8 children,
+ *                      Sec. 6) in a full-occupancy kernel of its own, one
+ *                      element per thread, before the tail; only elements
+ *                      that need deeper levels, or meet a sign FP32 cannot
+ *                      settle, go on to the tail's refinement.  Pays when
+ *                      many elements are decided on level 1 (boundary
+ *                      layers);
  *  HEXVAL_OPT_DFREDO   FP32 form: the escalations the FP32 pass leaves are
  *                      first redone in double-float (pairs of FP32 values,
  *                      about 44 bits, at FP32 throughput) by a kernel of its
@@ -128,7 +137,13 @@ typedef struct {
  *                      stream) that further identical calls launch: one
  *                      launch per call instead of three or more.  The
  *                      capture itself costs one host-side graph build. */
-enum { HEXVAL_OPT_PAIR32 = 1, HEXVAL_OPT_PREFETCH = 2, HEXVAL_OPT_DFREDO = 4, HEXVAL_OPT_NO_REPLAY = 8 };
+enum {
+  HEXVAL_OPT_PAIR32 = 1,
+  HEXVAL_OPT_PREFETCH = 2,
+  HEXVAL_OPT_DFREDO = 4,
+  HEXVAL_OPT_NO_REPLAY = 8,
+  HEXVAL_OPT_LEVEL1 = 16
+};
 
 typedef struct {
   uint64_t elements;        /* elements processed since the last reset */
@@ -136,8 +151,10 @@ typedef struct {
                                (double-float or FP64) */
   uint64_t refined;         /* elements that needed subdivision */
   uint64_t boxes;           /* boxes split by the refinement (root boxes
-                               included; the in-warp refinement of the FP32
-                               pass not counted) */
+                               included; boxes of elements settled on an
+                               earlier level are skipped, not counted; the
+                               in-warp FP64 refinement of the FP32 pass is
+                               not counted) */
   uint64_t exact;           /* elements decided by the exact tier */
   uint64_t max_level_boxes; /* largest refinement level (boxes) */
   uint64_t escalated_df;    /* of escalated_fp64: decided in double-float
@@ -153,7 +170,7 @@ int hexval_config_default(hexval_config* cfg);
 /* Creates a handle on cfg->device and allocates all of its device scratch
  * (about 485 B x queue_capacity + 16 B x max_nodes + 4 B x max_batch + 40 MB,
  * ~4.4 GB with the defaults; the FP32-filtered form adds about 225 B x
- * queue_capacity + 32 B x max_batch, ~2.4 GB).  Returns HEXVAL_E_NOMEM if
+ * queue_capacity + 36 B x max_batch, ~2.5 GB).  Returns HEXVAL_E_NOMEM if
  * that fails. */
 int hexval_create(const hexval_config* cfg, hexval_handle* out);
 
@@ -307,6 +324,7 @@ enum {
                             the exact tier (one launch) */
   HEXVAL_PH_EXACT = 4,   /* unused: the exact tier runs inside the tail */
   HEXVAL_PH_REDODF = 5,  /* double-float redo of escalations (HEXVAL_OPT_DFREDO) */
+  HEXVAL_PH_LEVEL1 = 6,  /* first refinement level in its own kernel (HEXVAL_OPT_LEVEL1) */
   HEXVAL_PH_COUNT = 8
 };
 typedef struct {

@@ -5,6 +5,8 @@
 //   [FP32 form, indexed]  nodes32 (once per call)
 //   bulk32 (FP32 form) or bulk64 (FP64 form) over all elements of the batch
 //   [FP32 form, HEXVAL_OPT_DFREDO]  redo_df: double-float redo of escalations
+//   [FP32 form, HEXVAL_OPT_LEVEL1]  level1: first refinement level of the
+//          elements listed for the FP32 refinement
 //   tail:  one cooperative launch that redoes the FP32 escalations in FP64,
 //          refines the undecided elements level by level, runs the exact
 //          tier, writes their verdicts and resets the batch counters.
@@ -125,6 +127,7 @@ const char* phase_name(int ph) {
     case HEXVAL_PH_BULK64: return "hexval bulk64";
     case HEXVAL_PH_TAIL: return "hexval tail";
     case HEXVAL_PH_REDODF: return "hexval redo_df";
+    case HEXVAL_PH_LEVEL1: return "hexval level1";
     default: return "hexval";
   }
 }
@@ -157,6 +160,8 @@ int run_batches(hexval_ctx* h, Batch p, int64_t n_hex, cudaStream_t st) {
                          : phase(h, HEXVAL_PH_BULK64, st, [&] { return hexval::launch_bulk64(p, st); });
     if (e == cudaSuccess && fp32 && p.dfredo)
       e = phase(h, HEXVAL_PH_REDODF, st, [&] { return hexval::launch_redo_df(p, st); });
+    if (e == cudaSuccess && fp32 && p.level1)
+      e = phase(h, HEXVAL_PH_LEVEL1, st, [&] { return hexval::launch_level1(p, st); });
     if (e == cudaSuccess)
       e = phase(h, HEXVAL_PH_TAIL, st,
                 [&] { return hexval::launch_tail(p, fp32, h->spin_limit, st); });
@@ -268,7 +273,7 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
       cfg->queue_capacity > (1ull << 31) || cfg->exact_capacity == 0 ||
       cfg->exact_capacity > (1ull << 31) || cfg->max_nodes > (1ull << 31) ||
       (cfg->options & ~static_cast<uint32_t>(HEXVAL_OPT_PAIR32 | HEXVAL_OPT_PREFETCH | HEXVAL_OPT_DFREDO |
-                                             HEXVAL_OPT_NO_REPLAY)) ||
+                                             HEXVAL_OPT_NO_REPLAY | HEXVAL_OPT_LEVEL1)) ||
       cfg->reserved || cfg->reserved2 || cfg->tail_warp_items < 1 || cfg->tail_warp_items > 64 ||
       (cfg->bulk_threads != 0 && cfg->bulk_threads != 64 && cfg->bulk_threads != 128 &&
        cfg->bulk_threads != 256))
@@ -309,7 +314,7 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
          alloc(h, &s.s32_lev, cfg->max_batch) && alloc(h, &s.s32_e0, cfg->max_batch) &&
          alloc(h, &s.s32_m0, cfg->max_batch) &&
          alloc(h, &s.iw, static_cast<uint64_t>(hexval::kIwSlots) * 2 * 27 * hexval::kIwBoxes) &&
-         alloc(h, &s.esc3, cfg->max_batch);
+         alloc(h, &s.esc3, cfg->max_batch) && alloc(h, &s.r32b, cfg->max_batch);
   }
   if (!ok) {
     free_all(h);
@@ -356,6 +361,7 @@ int hexval_check_soa(hexval_handle h, int64_t n_hex, const double* corners, uint
   p.indexed = 0;
   p.pair32 = (h->cfg.options & HEXVAL_OPT_PAIR32) != 0;
   p.dfredo = (h->cfg.options & HEXVAL_OPT_DFREDO) != 0;
+  p.level1 = (h->cfg.options & HEXVAL_OPT_LEVEL1) != 0;
   p.bulk_threads = static_cast<int>(h->cfg.bulk_threads);
   p.esc_in_pass = h->cfg.esc_in_pass;
   p.r32_in_pass = h->cfg.refine_in_pass;
@@ -388,6 +394,7 @@ int hexval_check_indexed(hexval_handle h, int64_t n_nodes, const double* nodes, 
   p.pair32 = (h->cfg.options & HEXVAL_OPT_PAIR32) != 0;
   p.prefetch32 = (h->cfg.options & HEXVAL_OPT_PREFETCH) != 0;
   p.dfredo = (h->cfg.options & HEXVAL_OPT_DFREDO) != 0;
+  p.level1 = (h->cfg.options & HEXVAL_OPT_LEVEL1) != 0;
   p.bulk_threads = static_cast<int>(h->cfg.bulk_threads);
   p.esc_in_pass = h->cfg.esc_in_pass;
   p.r32_in_pass = h->cfg.refine_in_pass;

@@ -71,7 +71,10 @@ struct Counters {
   unsigned int esc3_count;                  // double-float redo -> tail (list esc3)
   unsigned int df_count;                    // decided by the double-float redo
   unsigned int xb_count;                    // exact-check list (boxes)
-  unsigned int pad[1];
+  unsigned int l1_count;                    // elements the first-level kernel split
+  unsigned int r32b_count;                  // of those, left undecided (list r32b)
+  unsigned int split64;                     // FP64 boxes split by the refinement
+  unsigned int split32;                     // FP32 boxes split by the refinement
 };
 
 // Escalations of the FP32 pass: the first Batch::esc_in_pass elements
@@ -153,6 +156,8 @@ struct Scratch {
   double* iw;
   // FP32 form: elements the double-float redo leaves to FP64 (redo_df.cu)
   uint32_t* esc3;
+  // FP32 form: elements the first-level kernel leaves to the tail (level1.cu)
+  uint32_t* r32b;
 };
 
 // One batch of elements, as seen by every kernel.
@@ -170,6 +175,7 @@ struct Batch {
   int bulk_threads;  // block size of the bulk kernels (0: default)
   int prefetch32;    // indexed FP32 pass on a persistent grid with prefetch
   int dfredo;        // FP32 form: escalations redone in double-float first
+  int level1;        // FP32 form: first refinement level in a kernel of its own
   unsigned int esc_in_pass;  // FP32 escalations of a batch redone in FP64 by the FP32 pass
   unsigned int r32_in_pass;  // elements to refine redone in FP64 by the FP32 pass
   unsigned int warp_items;   // tail: warp-per-item steps up to this many items per warp
@@ -611,6 +617,9 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned int grid, unsig
 // FP32 form with HEXVAL_OPT_DFREDO: double-float redo of the escalations
 // the FP32 pass leaves (between the bulk and tail kernels).
 cudaError_t launch_redo_df(const Batch& p, cudaStream_t st);
+// FP32 form with HEXVAL_OPT_LEVEL1: the first refinement level of the
+// elements the FP32 pass lists for the FP32 refinement (before the tail).
+cudaError_t launch_level1(const Batch& p, cudaStream_t st);
 cudaError_t launch_quads(const QuadBatch& p, bool fp32, cudaStream_t st);
 cudaError_t launch_quality(const Batch& p, float* sj, cudaStream_t st);
 cudaError_t launch_minj(const Batch& p, double rel_tol, int max_depth, double* lo, double* hi,

@@ -27,14 +27,103 @@ __device__ __forceinline__ void split5f(float p0, float p1, float p2, float q[5]
   q[4] = p2;
 }
 
-// Root box of the i-th element left in the refinement list (list entry
-// r32_in_pass + i; slot i, box i of level 0): the FP32
-// coefficients recomputed exactly as the FP32 pass computed them, with their
-// bound.  Slots beyond the queue capacity are marked for the FP64 redo.
+// The first level of the FP32 refinement of one element, by one thread
+// (level1_kernel, HEXVAL_OPT_LEVEL1): its root box (the 27 depth-0
+// coefficients s in tensor order, as root32 stores them, M0 = max(|lo|,
+// |hi|) + E0 as root32 forms it) is split exactly as refine_box32 splits a
+// level-0 box, with the same bound E0 + 2^-20 M0 and the same
+// classification of the 8 children.  Returns the flag byte when level 1
+// decides the element -- a child corner certainly <= 0 (INVALID@1), all
+// children certified (VALID@1), or uncertified children at a depth cap of 1
+// (UNDECIDED) -- and -1 when it needs deeper levels or meets a sign FP32
+// cannot settle; the element then goes on to the tail's FP32 refinement,
+// which reaches the same verdict from the same root box.
+__device__ __forceinline__ int refine1_fp32(const Scaled<float>& s, float E0, float lo, float hi,
+                                            int max_depth) {
+  float A[27];
+  store_tensor(s, A);
+  const float M0 = fmaxf(fabsf(lo), fabsf(hi)) + E0;
+  const float E = fmaf(0x1p-20f, M0, E0);
+  const uint32_t key = fbits(E);
+  float P1[5][3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float q[5];
+      split5f(A[tix(0, j, k)], A[tix(1, j, k)], A[tix(2, j, k)], q);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) P1[i][j][k] = q[i];
+    }
+  float P2[5][5][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      float q[5];
+      split5f(P1[i][0][k], P1[i][1][k], P1[i][2][k], q);
+#pragma unroll
+      for (int j = 0; j < 5; ++j) P2[i][j][k] = q[j];
+    }
+  float G[5][5][5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) split5f(P2[i][j][0], P2[i][j][1], P2[i][j][2], G[i][j]);
+  bool invalid = false, open = false, capped = false;
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
+    bool nonpos = false, amb = false, notcert = false, amb2 = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const Sign3 q = sign_f(G[sx + i][sy + j][sz + k], key);
+          if ((i != 1) && (j != 1) && (k != 1)) {
+            nonpos |= q.nonpos;
+            amb |= !(q.nonpos | q.pos);
+          } else {
+            notcert |= q.nonpos;
+            amb2 |= !(q.nonpos | q.pos);
+          }
+        }
+    if (nonpos) {
+      invalid = true;
+    } else if (amb) {
+      open = true;  // the FP32 refinement would send the element to FP64
+    } else if (notcert) {
+      if (max_depth <= 1)
+        capped = true;
+      else
+        open = true;  // a child to queue for level 2
+    } else if (amb2) {
+      open = true;
+    }
+  }
+  if (invalid) return make_flag(kVInvalid, 1, 0);
+  if (open) return -1;
+  if (capped) return make_flag(kVUndecided, max_depth, 0);
+  return make_flag(kVValid, 1, 0);
+}
+
+// The elements the FP32 refinement of the tail works on: the refinement list
+// from entry r32_in_pass on, or, after the first-level kernel
+// (HEXVAL_OPT_LEVEL1), the list r32b of those it left undecided.
+__device__ __forceinline__ const uint32_t* refine_list(const Batch& p) {
+  return p.level1 ? p.s.r32b : p.s.r32 + p.r32_in_pass;
+}
+
+// Root box of the i-th element of refine_list (slot i, box i of level 0):
+// the FP32 coefficients recomputed exactly as the FP32 pass computed them,
+// with their bound.  Slots beyond the queue capacity are marked for the FP64
+// redo.
 __device__ __forceinline__ void root32(const Batch& p, bool act, unsigned int i) {
   if (!act) return;
   const Scratch& S = p.s;
-  const uint32_t e = ldcg(S.r32 + p.r32_in_pass + i);
+  const uint32_t e = ldcg(refine_list(p) + i);
   V3<float> Y[8];
   float X, E = 0.f, lo = 0.f, hi = 0.f;
   bool bad;
@@ -67,6 +156,11 @@ __device__ __forceinline__ void refine_box32(const Batch& p, int level, bool act
   const bool last = child_level >= p.max_depth;
   const uint32_t slot = act ? ldcg(S.q32slot[in] + idx) : 0u;
   if (act) act = !(ldcg(S.s32_state + slot) & (kStInvalid | kStAmbig | kStOverflow));
+  {  // boxes split, one atomic per warp
+    const unsigned int m = __ballot_sync(0xffffffffu, act);
+    if (m && (threadIdx.x & 31u) == static_cast<unsigned int>(__ffs(m) - 1))
+      atomicAdd(&S.cnt->split32, static_cast<unsigned int>(__popc(m)));
+  }
   float G[5][5][5];
   uint32_t key = 0;
   if (act) {

@@ -77,6 +77,11 @@ __device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool ac
   if (slot & kDeadBox) act = false;  // certified by the exact check
   slot &= ~kDeadBox;
   if (act) act = !(ldcg(S.slot_state + slot) & (kStInvalid | kStAmbig | kStOverflow));
+  {  // boxes split, one atomic per warp
+    const unsigned int m = __ballot_sync(0xffffffffu, act);
+    if (m && (threadIdx.x & 31u) == static_cast<unsigned int>(__ffs(m) - 1))
+      atomicAdd(&S.cnt->split64, static_cast<unsigned int>(__popc(m)));
+  }
   // exact check of uncertain children possible (box positions kept)
   const bool xok = S.xb_cap != 0 && S.qpos[in] != nullptr;
   const uint64_t ppos = (act && xok) ? ldcg(S.qpos[in] + idx) : 0ull;
@@ -414,11 +419,9 @@ __device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned in
       c = ldcg(&C->level_count[t]);
       c32 = ldcg(&C->level32_count[t]);
     }
-    unsigned long long boxes = c + c32, b32 = c32, mx = c > c32 ? c : c32;
+    unsigned long long mx = c > c32 ? c : c32;
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) {
-      boxes += __shfl_xor_sync(0xffffffffu, boxes, d);
-      b32 += __shfl_xor_sync(0xffffffffu, b32, d);
       const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, d);
       mx = o > mx ? o : mx;
     }
@@ -428,12 +431,15 @@ __device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned in
       atomicAdd(&st->elements, static_cast<unsigned long long>(p.n));
       atomicAdd(&st->escalated_fp64, static_cast<unsigned long long>(ldcg(&C->esc_count)) +
                                          ldcg(&C->esc2_count) + nr_here);
+      const unsigned int n1 = ldcg(&C->l1_count);
       atomicAdd(&st->refined, static_cast<unsigned long long>(ldcg(&C->level_count[0])) +
                                   (nr - nr_here) + ldcg(&C->iw_done));
-      // box expansions: the root boxes of the refined elements count too
-      // (FP64 roots in level_count[0], FP32 roots in the refinement list)
-      atomicAdd(&st->boxes, boxes + ldcg(&C->level_count[0]) + (nr - nr_here));
-      atomicAdd(&st->boxes_fp32, b32 + (nr - nr_here));
+      // boxes actually split (root boxes included; a box whose element was
+      // settled on an earlier level is skipped and not counted), and the
+      // root boxes the first-level kernel split
+      const unsigned long long s32 = static_cast<unsigned long long>(ldcg(&C->split32)) + n1;
+      atomicAdd(&st->boxes, static_cast<unsigned long long>(ldcg(&C->split64)) + s32);
+      atomicAdd(&st->boxes_fp32, s32);
       atomicAdd(&st->exact, static_cast<unsigned long long>(nx));
       atomicAdd(&st->escalated_df, static_cast<unsigned long long>(ldcg(&C->df_count)));
       atomicMax(&st->max_level_boxes, mx);
@@ -457,9 +463,12 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
   const unsigned int n_esc = !from_list ? 0u
                              : p.dfredo ? ldcg(&C->esc3_count)
                                         : (n_list > p.esc_in_pass ? n_list - p.esc_in_pass : 0u);
-  // refinement list entries [r32_in_pass, n_rl) are left for this kernel
+  // refinement list entries [r32_in_pass, n_rl) are left for this kernel,
+  // or, after the first-level kernel, the r32b list it leaves
   const unsigned int n_rl = from_list ? ldcg(&C->r32_count) : 0u;
-  const unsigned int n_r = n_rl > p.r32_in_pass ? n_rl - p.r32_in_pass : 0u;
+  const unsigned int n_r = !from_list ? 0u
+                           : p.level1 ? ldcg(&C->r32b_count)
+                                      : (n_rl > p.r32_in_pass ? n_rl - p.r32_in_pass : 0u);
   if (n_esc == 0 && n_r == 0 && ldcg(&C->level_count[0]) == 0 && ldcg(&C->exact_count) == 0) {
     // nothing left: every block reads only counters that are, or become,
     // zero here, so block 0 may end the batch at once

@@ -441,6 +441,7 @@ static __device__ __noinline__ void refine_box_warp(const Batch& p, int level, u
   if (sraw & kDeadBox) return;  // certified by the exact check
   const uint32_t slot = sraw;
   if (ldcg(S.slot_state + slot) & (kStInvalid | kStAmbig | kStOverflow)) return;
+  if (lane == 0) atomicAdd(&S.cnt->split64, 1u);
   const bool xok = S.xb_cap != 0 && S.qpos[in] != nullptr;
   const uint64_t ppos = xok ? ldcg(S.qpos[in] + idx) : 0ull;
   double* A = sm;          // [i + 3 j + 9 k]

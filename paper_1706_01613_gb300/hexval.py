@@ -24,6 +24,7 @@ OPT_PAIR32 = 1    # hexval_config.options: packed f32x2 FP32 bulk pass
 OPT_PREFETCH = 2  # hexval_config.options: persistent indexed FP32 pass with prefetch
 OPT_DFREDO = 4    # hexval_config.options: double-float redo of FP32 escalations
 OPT_NO_REPLAY = 8 # hexval_config.options: no graph replay of repeated check calls
+OPT_LEVEL1 = 16   # hexval_config.options: first refinement level in a kernel of its own
 VALID, INVALID, UNDECIDED, NONFINITE = 1, 2, 3, 4
 
 # every function declared in include/hexval.h (the CPU test checks the list)
@@ -34,7 +35,7 @@ EXPORTS = ("hexval_config_default", "hexval_create", "hexval_destroy", "hexval_c
            "hexval_corner_quality_indexed", "hexval_compact", "hexval_min_jacobian",
            "hexval_min_jacobian_indexed", "hexval_strerror", "hexval_scratch_bytes",
            "hexval_copy_soa_range")
-PHASES = ("nodes32", "bulk32", "bulk64", "tail", "-", "redo_df", "-", "-")
+PHASES = ("nodes32", "bulk32", "bulk64", "tail", "-", "redo_df", "level1", "-")
 
 
 class Config(ctypes.Structure):
@@ -146,7 +147,7 @@ class Validator:
     of the default configuration (max_depth, queue_capacity, max_batch,
     max_nodes, exact_capacity, bulk_threads, esc_in_pass, refine_in_pass,
     tail_warp_items, options = OPT_* bits: PAIR32, PREFETCH, DFREDO,
-    NO_REPLAY).  Repeated identical check calls are
+    NO_REPLAY, LEVEL1).  Repeated identical check calls are
     replayed from a CUDA graph unless NO_REPLAY is set."""
 
     def __init__(self, precision="fp64", max_depth=8, device=None, **caps):

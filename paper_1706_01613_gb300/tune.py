@@ -3,8 +3,9 @@
 For a workload shape (precision, input kind, size) it times every candidate
 launch configuration of the handle (FP32 bulk pass scalar, staged or packed
 f32x2; bulk block size; for the FP64 form the block size), re-times the
-leaders, then tries on the winner the double-float redo of escalations
-(FP32 form) and, one knob at a time, the placement of the uneven work: how
+leaders, then tries on the winner the double-float redo of escalations and
+the FP32 pass's own first refinement level (FP32 form) and, one knob at a
+time, the placement of the uneven work: how
 many FP32 escalations and elements to refine the bulk pass keeps for itself
 (esc_in_pass, refine_in_pass) and the tail kernel's threshold between
 one item per warp and one per thread (tail_warp_items).  Timing is on a
@@ -119,12 +120,14 @@ def best_config(precision, kind, n, dev_inputs, cache=CACHE, retune=False, reps=
     best_ms, best = final[0]
     if precision == "fp32":
         # the double-float redo pays off only when many elements escalate,
-        # which depends on the data: tried on the winner
-        dfr = dict(best, options=best["options"] | hv.OPT_DFREDO)
-        ms = time_config(dfr, precision, kind, dev_inputs, reps=3 * reps, **caps)
-        results.append((ms, dfr))
-        if ms < best_ms:
-            best_ms, best = ms, dfr
+        # and the pass's own first refinement level when many elements are
+        # decided there, which depends on the data: each tried on the winner
+        for opt in (hv.OPT_DFREDO, hv.OPT_LEVEL1):
+            trial = dict(best, options=best["options"] | opt)
+            ms = time_config(trial, precision, kind, dev_inputs, reps=3 * reps, **caps)
+            results.append((ms, trial))
+            if ms < best_ms:
+                best_ms, best = ms, trial
     best = dict(best)
     for name, values in KNOBS[precision]:
         best.setdefault(name, values[0])

@@ -550,7 +550,8 @@ def test_autotuner_picks_a_candidate_and_stays_exact(tmp_path):
     dev = (torch.from_numpy(nodes).cuda(), torch.from_numpy(conn).cuda())
     cache = str(tmp_path / "tune.json")
     best = tune.best_config("fp32", "indexed", len(conn), dev, cache=cache, reps=3, **CAPS)
-    launch = {"options": best["options"] & ~hv.OPT_DFREDO, "bulk_threads": best["bulk_threads"]}
+    launch = {"options": best["options"] & ~(hv.OPT_DFREDO | hv.OPT_LEVEL1),
+              "bulk_threads": best["bulk_threads"]}
     assert launch in tune.candidates("fp32")
     assert tune.best_config("fp32", "indexed", len(conn), dev, cache=cache, **CAPS) == best
     v = hv.Validator(precision="fp32", max_depth=8, **best, **CAPS)
@@ -668,3 +669,32 @@ def test_copy_soa_range_from_host_and_device():
         assert torch.equal(dst.cpu(), X[:, :, 2345:2345 + 1234])
     with pytest.raises(hv.HexvalError):
         hv.copy_soa_range(torch.empty((8, 3, 10), dtype=torch.float64, device="cuda"), X, 4995)
+
+
+@pytest.mark.parametrize("opt", [hv.OPT_LEVEL1, hv.OPT_LEVEL1 | hv.OPT_PAIR32,
+                                 hv.OPT_LEVEL1 | hv.OPT_PREFETCH])
+def test_first_level_in_the_fp32_pass(opt):
+    """HEXVAL_OPT_LEVEL1: elements decided on level 1 by the first-level
+    kernel (boundary-layer prisms, about a quarter need one level), the
+    others by the tail as before; flags equal to the default's and the
+    oracle's, depth caps 1 and 10; the statistics count them as refined."""
+    X = synth.twisted_layers(30_000, seed=20170015, theta_max_deg=150.0)
+    for depth in (1, 10):
+        base = hv.Validator(precision="fp32", max_depth=depth, **CAPS)
+        want = _run_soa(base, X)
+        v = hv.Validator(precision="fp32", max_depth=depth, options=opt, **CAPS)
+        v.stats(reset=True)
+        got = _run_soa(v, X)
+        st = v.stats()
+        assert got[3] == 0
+        assert np.array_equal(got[0] & 0x7F, want[0] & 0x7F)
+        _compare("fp32", got[:3], oracle.check_soa(X, max_depth=depth), X)
+        assert st["refined"] >= ((want[0] >> 3 & 15) >= 1).sum()
+        base.close()
+        v.close()
+    nodes, conn = synth.structured_grid(20, 18, 16, sigma=0.35, seed=20170016)
+    v = hv.Validator(precision="fp32", max_depth=8, options=opt, **CAPS)
+    got = [t.cpu().numpy() for t in v.check_indexed(torch.from_numpy(nodes).cuda(),
+                                                    torch.from_numpy(conn).cuda())]
+    _compare("fp32", got, oracle.check_indexed(nodes, conn, max_depth=8), _soa(nodes, conn))
+    v.close()

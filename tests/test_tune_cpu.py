@@ -37,10 +37,11 @@ def test_fastest_leader_is_kept_and_cached(stub, tmp_path):
     assert best == dict(options=hv.OPT_PREFETCH, bulk_threads=128, **defaults)
     n_cand = len(tune.candidates("fp32"))
     n_knob = sum(len(v) - 1 for _, v in tune.KNOBS["fp32"])
-    # all, the three leaders again, the redo trial, the knob trials
-    assert len(calls) == n_cand + 3 + 1 + n_knob
+    # all, the three leaders again, the redo and first-level trials, the knob trials
+    assert len(calls) == n_cand + 3 + 2 + n_knob
     assert all(r == 60 for _, r in calls[n_cand:])
     assert calls[n_cand + 3][0] == {"options": hv.OPT_PREFETCH | hv.OPT_DFREDO, "bulk_threads": 128}
+    assert calls[n_cand + 4][0] == {"options": hv.OPT_PREFETCH | hv.OPT_LEVEL1, "bulk_threads": 128}
     data = json.load(open(cache))
     assert data["dev|fp32|indexed|1000"]["config"] == best
     calls.clear()
