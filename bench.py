@@ -259,14 +259,20 @@ def traffic_for(kernel):
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_1706_01613_gb300", "csrc", rec["source"])
-    h = hashlib.sha256()
-    for part in [src, os.path.join(ROOT, "paper_1706_01613_gb300", "csrc", "hexval_internal.cuh")]:
-        with open(part, "rb") as f:
-            h.update(f.read())
-    if h.hexdigest()[:16] != rec.get("source_sha"):
+    if source_sha(rec["source"]) != rec.get("source_sha"):
         return None
     return rec["dram_bytes_per_launch"]
+
+
+def source_sha(source):
+    """Hash of a kernel's source file and every header of the CUDA sources
+    (any of which it may include)."""
+    csrc = os.path.join(ROOT, "paper_1706_01613_gb300", "csrc")
+    h = hashlib.sha256()
+    for part in [source] + sorted(f for f in os.listdir(csrc) if f.endswith(".cuh")):
+        with open(os.path.join(csrc, part), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def peaks():
@@ -431,6 +437,48 @@ def filter_run(steps, warmup, flush):
             "value": n / (ms / 1e3), "unit": "candidate/s", "ms_per_call": ms, "kept": kept}
 
 
+def quality_run(w, dev_in, steps, warmup, flush):
+    """Corner scaled Jacobian (Sec. 7's quality measure) on the benchmark
+    mesh, per call with CUDA events, L2 flushed; HBM roofline on the bytes
+    it must move (connectivity 32 B and output 4 B per element, 24 B per
+    FP64 node)."""
+    import torch
+    from paper_1706_01613_gb300 import hexval as hv
+    v = hv.Validator(precision="fp64", queue_capacity=1 << 10, max_batch=1 << 10,
+                     max_nodes=1 << 10, exact_capacity=1 << 10)
+    out = torch.empty(w["n"], dtype=torch.float32, device="cuda")
+
+    def call():
+        if w["kind"] == "indexed":
+            v.corner_quality_indexed(dev_in[0], dev_in[1], out=out)
+        else:
+            v.corner_quality(dev_in[0], out=out)
+
+    for _ in range(warmup):
+        flush.zero_()
+        call()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record()
+        call()
+        b.record()
+    torch.cuda.synchronize()
+    v.raise_on_status()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    v.close()
+    abytes = (32 + 4) * w["n"] + 24 * w["n_nodes"] if w["kind"] == "indexed" else 196 * w["n"]
+    hbm, kind = peaks()
+    achieved = abytes / (ms / 1e3) / 1e9
+    return {"workload": w["name"], "value": w["n"] / (ms / 1e3), "unit": "hex/s",
+            "ms_per_call": ms,
+            "roofline": {"bound": "hbm", "kernel": "quality", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm,
+                         "peak_kind": kind + " (hbm_gbs)", "algorithmic_bytes_per_launch": abytes,
+                         "traffic": None}}
+
+
 def minj_run(w, dev_in, steps, warmup, flush, rel_tol=1e-6, max_depth=12):
     """Minimum of J to a tolerance on the benchmark mesh (FP64 branch and
     bound on the coefficients), per call with CUDA events, L2 flushed."""
@@ -463,9 +511,11 @@ def minj_run(w, dev_in, steps, warmup, flush, rel_tol=1e-6, max_depth=12):
             "mean_levels": float((d & 0x7F).mean()), "not_converged": int((d & 0x80).astype(bool).sum())}
 
 
-def serving_run(precision, rate, n_requests, pool, slots=4, budget=40 << 30, seed=20175000):
+def serving_run(precision, rate, n_requests, pool, slots=5, budget=40 << 30, seed=20175000,
+                small_slots=1, small_n=100_000):
     """One continuous-batching run: Poisson arrivals at `rate`/s, sizes
-    log-uniform in [100, pool size]; returns the latency summary."""
+    log-uniform in [100, pool size], `small_slots` of the slots kept for
+    requests of at most `small_n` elements; returns the latency summary."""
     from paper_1706_01613_gb300 import serve
     reqs = serve.poisson_stream(pool, n_requests, rate, seed=seed + int(rate),
                                 size_max=pool.max_n)
@@ -473,13 +523,16 @@ def serving_run(precision, rate, n_requests, pool, slots=4, budget=40 << 30, see
                            queue_capacity=1 << 21, max_batch=1 << 24, max_nodes=1 << 24,
                            exact_capacity=1 << 14)
     try:
-        sched = serve.run_stream(reqs, ex, slots=slots, budget_bytes=budget)
+        sched = serve.run_stream(reqs, ex, slots=slots, budget_bytes=budget,
+                                 small_slots=small_slots, small_n=small_n)
         bad = [s for s in ex.status() if s != 0]
     finally:
         ex.close()
     out = serve.latency_summary(reqs)
     out.update({"rate_per_s": rate, "rejected": len(sched.rejected), "status_errors": len(bad),
-                "precision": precision, "slots": slots, "hbm_budget_gb": budget / 2**30})
+                "precision": precision, "slots": slots, "hbm_budget_gb": budget / 2**30,
+                "slots_for_short_requests": small_slots, "short_request_max_n": small_n,
+                "slot_scratch_gb": ex.fixed_bytes / 2**30})
     return out
 
 
@@ -743,6 +796,7 @@ def main():
     quads = quad_run(max(5, args.steps // 20), 3, flush) if args.quads else None
     filt = filter_run(max(5, args.steps // 50), 3, flush) if args.quads else None
     mj = minj_run(w, dev_in, 5, 2, flush) if args.quads else None
+    qual = quality_run(w, dev_in, max(5, args.steps // 50), 3, flush) if args.quads else None
 
     # the other configurations (device-resident, both forms) and the serving
     # stream of the scope table: 10,000 requests, sizes log-uniform in
@@ -793,6 +847,7 @@ def main():
         "quads": quads,
         "filter": filt,
         "min_jacobian": mj,
+        "corner_quality": qual,
         "clocks": clocks.summary(*window),
     }
     print(json.dumps(rec))

@@ -464,6 +464,80 @@ __device__ __forceinline__ float pow2f(int p) {
   return __uint_as_float(static_cast<uint32_t>(e) << 23);
 }
 
+// ------------------------------------------------ unscaled box splitting ----
+// The quadratic de Casteljau split of a row (p0, p1, p2) at 1/2 is
+// (p0, s/2, (s+t)/4, t/2, p2) with s = p0 + p1, t = p1 + p2 (Sec. 6).  The
+// refinement computes it unscaled, (p0, s, s+t, t, p2): entry x carries the
+// factor 2^c(x), c = (0, 1, 2, 1, 0), and costs 3 additions per row instead
+// of 6 operations.  The scalings being exact, every unscaled entry is exactly
+// 2^c times the halved one (no overflow: |p| <= M keeps every entry of a
+// box's three passes within 64 M).  After the three passes entry
+// (x, y, z) of the 5x5x5 grid carries 2^(c(x)+c(y)+c(z)), which the sign
+// tests take into account (sign_*_split) and the children are stored
+// without (down2 / down2f).
+__host__ __device__ constexpr int split_exp(int x) { return x < 2 ? x : 4 - x; }
+__host__ __device__ constexpr int split_exp3(int x, int y, int z) {
+  return split_exp(x) + split_exp(y) + split_exp(z);
+}
+
+// sign_d / sign_f of the value 2^-m v against the key of E, v carrying the
+// factor 2^m: the magnitude's exponent field less m, compared as a signed
+// integer (a magnitude below 2^m is never certain).  The same test as
+// sign_*(2^-m v, key) for a normal 2^-m v; for a subnormal one it is as
+// conservative (its magnitude is below every normal E).  Needs key + (m <<
+// 20) (FP32: m << 23) < 2^31, which the range of M0 the split runs in
+// (split_range_ok, E <= M0) guarantees.
+__device__ __forceinline__ Sign3 sign_d_split(double v, uint32_t ekey, int m) {
+  const uint32_t h = dhi(v);
+  const bool big = static_cast<int>((h & 0x7fffffffu) - (static_cast<uint32_t>(m) << 20)) >
+                   static_cast<int>(ekey);
+  return {big && (h >> 31), big && !(h >> 31)};
+}
+__device__ __forceinline__ Sign3 sign_f_split(float v, uint32_t ekey, int m) {
+  const uint32_t h = fbits(v);
+  const bool big = static_cast<int>((h & 0x7fffffffu) - (static_cast<uint32_t>(m) << 23)) >
+                   static_cast<int>(ekey);
+  return {big && (h >> 31), big && !(h >> 31)};
+}
+
+// 2^-m u for 0 <= m <= 6 by exponent arithmetic on the integer pipe: exact
+// when the result is normal; a result below the normal range becomes a zero
+// of u's sign (absolute error < 2^-1022, FP32: < 2^-126).
+__device__ __forceinline__ double down2(double u, int m) {
+  const long long b = __double_as_longlong(u);
+  const uint32_t e = (static_cast<uint32_t>(b >> 32) >> 20) & 0x7ffu;
+  return __longlong_as_double(e > static_cast<uint32_t>(m) ? b - (static_cast<long long>(m) << 52)
+                                                           : b & (1LL << 63));
+}
+__device__ __forceinline__ float down2f(float u, int m) {
+  const uint32_t b = __float_as_uint(u);
+  const uint32_t e = (b >> 23) & 0xffu;
+  return __uint_as_float(e > static_cast<uint32_t>(m) ? b - (static_cast<uint32_t>(m) << 23)
+                                                      : b & 0x80000000u);
+}
+
+// Range of the root magnitude bound M0 in which the unscaled split runs; a
+// box of an element outside it is left to the next tier.  Above: 64 M0 stays
+// finite.  Below: the per-level bound d 2^-49 M0 (FP32: d 2^-20 M0) allows
+// 16 roundings of u M0 per level where a split makes at most 6, and the
+// other 10 u M0 cover the flush of down2 (2^-1022 <= 2^-62 M0 for M0 >=
+// 2^-960; 2^-126 <= 2^-26 M0 for M0 >= 2^-100).
+constexpr double kSplitMaxM0 = 0x1p1000;
+constexpr double kSplitMinM0 = 0x1p-960;
+constexpr float kSplitMaxM0f = 0x1p120f;
+constexpr float kSplitMinM0f = 0x1p-100f;
+
+// M0 within that range (integer compares of the bit patterns, M0 >= 0)
+__device__ __forceinline__ bool split_range_ok(double m0) {
+  const uint32_t h = static_cast<uint32_t>(__double_as_longlong(m0) >> 32);
+  return h >= static_cast<uint32_t>(__double_as_longlong(kSplitMinM0) >> 32) &&
+         h < static_cast<uint32_t>(__double_as_longlong(kSplitMaxM0) >> 32);
+}
+__device__ __forceinline__ bool split_range_ok(float m0) {
+  const uint32_t b = __float_as_uint(m0);
+  return b >= __float_as_uint(kSplitMinM0f) && b < __float_as_uint(kSplitMaxM0f);
+}
+
 // Biased exponent of the largest |component| among the 12 edge vectors
 // (integer max over the high words).
 __device__ __forceinline__ int max_exponent_d(const V3<double> a[4], const V3<double> b[4],

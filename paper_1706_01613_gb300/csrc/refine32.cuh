@@ -2,7 +2,8 @@
 // to need subdivision (all 20 samples certainly positive, a coefficient
 // certainly non-positive) are refined breadth first with FP32 boxes, exactly
 // as the FP64 refinement of tail.cu (Sec. 6: split at 1/2 along xi, eta,
-// zeta by quadratic de Casteljau; a child with a corner certainly <= 0 makes
+// zeta by quadratic de Casteljau, computed unscaled as hexval_internal.cuh
+// describes; a child with a corner certainly <= 0 makes
 // the element INVALID at that level, a child with all 27 certainly > 0 is
 // certified, any other child is queued, or the depth cap is reached).
 // An element whose boxes meet a sign that the FP32 bound cannot settle, or
@@ -18,12 +19,13 @@
 
 namespace hexval {
 
-__device__ __forceinline__ void split5f(float p0, float p1, float p2, float q[5]) {
+// Unscaled split of a row (hexval_internal.cuh): entry x carries 2^c(x).
+__device__ __forceinline__ void split5uf(float p0, float p1, float p2, float q[5]) {
   const float s = p0 + p1, t = p1 + p2;
   q[0] = p0;
-  q[1] = 0.5f * s;
-  q[2] = 0.25f * (s + t);
-  q[3] = 0.5f * t;
+  q[1] = s;
+  q[2] = s + t;
+  q[3] = t;
   q[4] = p2;
 }
 
@@ -43,6 +45,7 @@ __device__ __forceinline__ int refine1_fp32(const Scaled<float>& s, float E0, fl
   float A[27];
   store_tensor(s, A);
   const float M0 = fmaxf(fabsf(lo), fabsf(hi)) + E0;
+  if (!split_range_ok(M0)) return -1;  // the tail sends it to FP64
   const float E = fmaf(0x1p-20f, M0, E0);
   const uint32_t key = fbits(E);
   float P1[5][3][3];
@@ -51,7 +54,7 @@ __device__ __forceinline__ int refine1_fp32(const Scaled<float>& s, float E0, fl
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       float q[5];
-      split5f(A[tix(0, j, k)], A[tix(1, j, k)], A[tix(2, j, k)], q);
+      split5uf(A[tix(0, j, k)], A[tix(1, j, k)], A[tix(2, j, k)], q);
 #pragma unroll
       for (int i = 0; i < 5; ++i) P1[i][j][k] = q[i];
     }
@@ -61,7 +64,7 @@ __device__ __forceinline__ int refine1_fp32(const Scaled<float>& s, float E0, fl
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
       float q[5];
-      split5f(P1[i][0][k], P1[i][1][k], P1[i][2][k], q);
+      split5uf(P1[i][0][k], P1[i][1][k], P1[i][2][k], q);
 #pragma unroll
       for (int j = 0; j < 5; ++j) P2[i][j][k] = q[j];
     }
@@ -69,7 +72,7 @@ __device__ __forceinline__ int refine1_fp32(const Scaled<float>& s, float E0, fl
 #pragma unroll
   for (int j = 0; j < 5; ++j)
 #pragma unroll
-    for (int i = 0; i < 5; ++i) split5f(P2[i][j][0], P2[i][j][1], P2[i][j][2], G[i][j]);
+    for (int i = 0; i < 5; ++i) split5uf(P2[i][j][0], P2[i][j][1], P2[i][j][2], G[i][j]);
   bool invalid = false, open = false, capped = false;
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
@@ -81,7 +84,8 @@ __device__ __forceinline__ int refine1_fp32(const Scaled<float>& s, float E0, fl
       for (int j = 0; j < 3; ++j)
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          const Sign3 q = sign_f(G[sx + i][sy + j][sz + k], key);
+          const Sign3 q = sign_f_split(G[sx + i][sy + j][sz + k],
+                                       key, split_exp3(sx + i, sy + j, sz + k));
           if ((i != 1) && (j != 1) && (k != 1)) {
             nonpos |= q.nonpos;
             amb |= !(q.nonpos | q.pos);
@@ -161,23 +165,25 @@ __device__ __forceinline__ void refine_box32(const Batch& p, int level, bool act
     if (m && (threadIdx.x & 31u) == static_cast<unsigned int>(__ffs(m) - 1))
       atomicAdd(&S.cnt->split32, static_cast<unsigned int>(__popc(m)));
   }
-  float G[5][5][5];
+  float G[5][5][5];  // unscaled: entry (x, y, z) carries 2^split_exp3(x, y, z)
   uint32_t key = 0;
+  uint32_t bits = 0;
   if (act) {
     const float* qc = S.q32coef[in];
     float A[27];
 #pragma unroll
     for (int t = 0; t < 27; ++t) A[t] = ldcg(qc + static_cast<uint64_t>(t) * S.q32cap + idx);
-    const float E = fmaf(static_cast<float>(child_level) * 0x1p-20f, ldcg(S.s32_m0 + slot),
-                         ldcg(S.s32_e0 + slot));
+    const float m0 = ldcg(S.s32_m0 + slot);
+    const float E = fmaf(static_cast<float>(child_level) * 0x1p-20f, m0, ldcg(S.s32_e0 + slot));
     key = fbits(E);
+    if (!split_range_ok(m0)) bits = kStAmbig;  // redone in FP64
     float P1[5][3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         float q[5];
-        split5f(A[tix(0, j, k)], A[tix(1, j, k)], A[tix(2, j, k)], q);
+        split5uf(A[tix(0, j, k)], A[tix(1, j, k)], A[tix(2, j, k)], q);
 #pragma unroll
         for (int i = 0; i < 5; ++i) P1[i][j][k] = q[i];
       }
@@ -187,17 +193,17 @@ __device__ __forceinline__ void refine_box32(const Batch& p, int level, bool act
 #pragma unroll
       for (int i = 0; i < 5; ++i) {
         float q[5];
-        split5f(P1[i][0][k], P1[i][1][k], P1[i][2][k], q);
+        split5uf(P1[i][0][k], P1[i][1][k], P1[i][2][k], q);
 #pragma unroll
         for (int j = 0; j < 5; ++j) P2[i][j][k] = q[j];
       }
 #pragma unroll
     for (int j = 0; j < 5; ++j)
 #pragma unroll
-      for (int i = 0; i < 5; ++i) split5f(P2[i][j][0], P2[i][j][1], P2[i][j][2], G[i][j]);
+      for (int i = 0; i < 5; ++i) split5uf(P2[i][j][0], P2[i][j][1], P2[i][j][2], G[i][j]);
   }
-  uint32_t bits = 0, queue = 0;
-  if (act) {
+  uint32_t queue = 0;
+  if (act && !bits) {
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
       const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
@@ -208,7 +214,8 @@ __device__ __forceinline__ void refine_box32(const Batch& p, int level, bool act
         for (int j = 0; j < 3; ++j)
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
-            const Sign3 q = sign_f(G[sx + i][sy + j][sz + k], key);
+            const Sign3 q = sign_f_split(G[sx + i][sy + j][sz + k],
+                                         key, split_exp3(sx + i, sy + j, sz + k));
             if ((i != 1) && (j != 1) && (k != 1)) {
               nonpos |= q.nonpos;
               amb |= !(q.nonpos | q.pos);
@@ -259,7 +266,8 @@ __device__ __forceinline__ void refine_box32(const Batch& p, int level, bool act
           for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int i = 0; i < 3; ++i)
-              dst[static_cast<uint64_t>(tix(i, j, k)) * S.q32cap + pos] = G[sx + i][sy + j][sz + k];
+              dst[static_cast<uint64_t>(tix(i, j, k)) * S.q32cap + pos] =
+                  down2f(G[sx + i][sy + j][sz + k], split_exp3(sx + i, sy + j, sz + k));
         S.q32slot[out][pos] = slot;
       } else {
         bits |= kStOverflow;

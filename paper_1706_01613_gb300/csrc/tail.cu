@@ -58,12 +58,13 @@ constexpr int kTailThreads = 128;
 #define HEXVAL_TAIL_INLINE __forceinline__
 #endif
 
-__device__ __forceinline__ void split5(double p0, double p1, double p2, double q[5]) {
-  double s = p0 + p1, t = p1 + p2;
+// Unscaled split of a row (hexval_internal.cuh): entry x carries 2^c(x).
+__device__ __forceinline__ void split5u(double p0, double p1, double p2, double q[5]) {
+  const double s = p0 + p1, t = p1 + p2;
   q[0] = p0;
-  q[1] = 0.5 * s;
-  q[2] = 0.25 * (s + t);
-  q[3] = 0.5 * t;
+  q[1] = s;
+  q[2] = s + t;
+  q[3] = t;
   q[4] = p2;
 }
 
@@ -85,23 +86,25 @@ __device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool ac
   // exact check of uncertain children possible (box positions kept)
   const bool xok = S.xb_cap != 0 && S.qpos[in] != nullptr;
   const uint64_t ppos = (act && xok) ? ldcg(S.qpos[in] + idx) : 0ull;
-  double G[5][5][5];
+  double G[5][5][5];  // unscaled: entry (x, y, z) carries 2^split_exp3(x, y, z)
   uint32_t key = 0;
+  uint32_t bits = 0;  // element state bits found by this box
   if (act) {
     const double* qc = S.qcoef[in];
     double A[27];
 #pragma unroll
     for (int t = 0; t < 27; ++t) A[t] = ldcg(qc + static_cast<uint64_t>(t) * S.qcap + idx);
-    double E = fma(static_cast<double>(child_level) * 0x1p-49, ldcg(S.slot_m0 + slot),
-                   ldcg(S.slot_e0 + slot));
+    const double m0 = ldcg(S.slot_m0 + slot);
+    double E = fma(static_cast<double>(child_level) * 0x1p-49, m0, ldcg(S.slot_e0 + slot));
     key = dhi(E);
+    if (!split_range_ok(m0)) bits = kStAmbig;  // the exact tier decides it
     double P1[5][3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         double q[5];
-        split5(A[tix(0, j, k)], A[tix(1, j, k)], A[tix(2, j, k)], q);
+        split5u(A[tix(0, j, k)], A[tix(1, j, k)], A[tix(2, j, k)], q);
 #pragma unroll
         for (int i = 0; i < 5; ++i) P1[i][j][k] = q[i];
       }
@@ -111,19 +114,18 @@ __device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool ac
 #pragma unroll
       for (int i = 0; i < 5; ++i) {
         double q[5];
-        split5(P1[i][0][k], P1[i][1][k], P1[i][2][k], q);
+        split5u(P1[i][0][k], P1[i][1][k], P1[i][2][k], q);
 #pragma unroll
         for (int j = 0; j < 5; ++j) P2[i][j][k] = q[j];
       }
 #pragma unroll
     for (int j = 0; j < 5; ++j)
 #pragma unroll
-      for (int i = 0; i < 5; ++i) split5(P2[i][j][0], P2[i][j][1], P2[i][j][2], G[i][j]);
+      for (int i = 0; i < 5; ++i) split5u(P2[i][j][0], P2[i][j][1], P2[i][j][2], G[i][j]);
   }
-  uint32_t bits = 0;   // element state bits found by this box
   uint32_t queue = 0;  // children to queue
   uint32_t xq = 0;     // children whose class an uncertain sign decides: exact check
-  if (act) {
+  if (act && !bits) {
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
       const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
@@ -134,7 +136,8 @@ __device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool ac
         for (int j = 0; j < 3; ++j)
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
-            Sign3 q = sign_d(G[sx + i][sy + j][sz + k], key);
+            Sign3 q = sign_d_split(G[sx + i][sy + j][sz + k],
+                                   key, split_exp3(sx + i, sy + j, sz + k));
             if ((i != 1) && (j != 1) && (k != 1)) {
               nonpos |= q.nonpos;
               amb |= !(q.nonpos | q.pos);
@@ -206,7 +209,8 @@ __device__ HEXVAL_TAIL_INLINE void refine_box(const Batch& p, int level, bool ac
           for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int i = 0; i < 3; ++i)
-              dst[static_cast<uint64_t>(tix(i, j, k)) * S.qcap + pos] = G[sx + i][sy + j][sz + k];
+              dst[static_cast<uint64_t>(tix(i, j, k)) * S.qcap + pos] =
+                  down2(G[sx + i][sy + j][sz + k], split_exp3(sx + i, sy + j, sz + k));
         S.qslot[out][pos] = slot;
         if (xok) S.qpos[out][pos] = cpos;
         qi = pos;

@@ -209,9 +209,22 @@ __device__ __forceinline__ void split5_row(const double* in, int stride_in, doub
   out[4 * stride_out] = p2;
 }
 
-// The three de Casteljau passes of a box whose 27 coefficients are in
-// sm[0..27) (tensor order): its 125 split values into sm[147..272), indexed
-// (i + 5 (j + 5 k)).  All lanes.
+// Unscaled split of a row (hexval_internal.cuh): entry x carries 2^c(x).
+__device__ __forceinline__ void split5u_row(const double* in, int stride_in, double* out,
+                                            int stride_out) {
+  const double p0 = in[0], p1 = in[stride_in], p2 = in[2 * stride_in];
+  const double s = p0 + p1, t = p1 + p2;
+  out[0] = p0;
+  out[stride_out] = s;
+  out[2 * stride_out] = s + t;
+  out[3 * stride_out] = t;
+  out[4 * stride_out] = p2;
+}
+
+// The three unscaled de Casteljau passes of a box whose 27 coefficients are
+// in sm[0..27) (tensor order): its 125 split values into sm[147..272),
+// indexed (i + 5 (j + 5 k)), value (i, j, k) carrying 2^split_exp3(i, j, k).
+// All lanes.
 __device__ __forceinline__ void split_box_warp(double* sm) {
   const int lane = threadIdx.x & 31;
   double* A = sm;        // [i + 3 j + 9 k]
@@ -221,23 +234,23 @@ __device__ __forceinline__ void split_box_warp(double* sm) {
   __syncwarp();
   if (lane < 9) {  // along xi: row (j, k)
     int j = lane % 3, k = lane / 3;
-    split5_row(A + 3 * j + 9 * k, 1, P1 + 5 * (j + 3 * k), 1);
+    split5u_row(A + 3 * j + 9 * k, 1, P1 + 5 * (j + 3 * k), 1);
   }
   __syncwarp();
   if (lane < 15) {  // along eta: row (i, k)
     int i = lane % 5, k = lane / 5;
-    split5_row(P1 + i + 15 * k, 5, P2 + i + 25 * k, 5);
+    split5u_row(P1 + i + 15 * k, 5, P2 + i + 25 * k, 5);
   }
   __syncwarp();
   if (lane < 25) {  // along zeta: row (i, j)
     int i = lane % 5, j = lane / 5;
-    split5_row(P2 + i + 5 * j, 25, G + i + 5 * j, 25);
+    split5u_row(P2 + i + 5 * j, 25, G + i + 5 * j, 25);
   }
   __syncwarp();
 }
 
-// Classification of child `o` (lane o < 8) of a split box against the bound
-// key: the state bits it contributes and whether it must be queued (as
+// Classification of child `o` (lane o < 8) of a box split by split_box_warp
+// against the bound key: the state bits it contributes and whether it must be queued (as
 // refine_box in tail.cu).
 __device__ __forceinline__ void classify_child_warp(const double* G, uint32_t key, bool last,
                                                     uint32_t& bits, bool& want) {
@@ -250,7 +263,8 @@ __device__ __forceinline__ void classify_child_warp(const double* G, uint32_t ke
   for (int k = 0; k < 3; ++k)
     for (int j = 0; j < 3; ++j)
       for (int i = 0; i < 3; ++i) {
-        Sign3 q = sign_d(G[(sx + i) + 5 * ((sy + j) + 5 * (sz + k))], key);
+        Sign3 q = sign_d_split(G[(sx + i) + 5 * ((sy + j) + 5 * (sz + k))],
+                               key, split_exp3(sx + i, sy + j, sz + k));
         if ((i != 1) && (j != 1) && (k != 1)) {
           nonpos |= q.nonpos;
           amb |= !(q.nonpos | q.pos);
@@ -277,7 +291,7 @@ static __device__ __noinline__ int refine_in_warp(const Batch& p, double un, dou
                                                   double* sm) {
   const Scratch& S = p.s;
   const int lane = threadIdx.x & 31;
-  if (!S.iw) return -1;
+  if (!S.iw || !split_range_ok(M0)) return -1;
   unsigned int slot = 0;
   if (lane == 0) slot = atomicAdd(&S.cnt->iw_count, 1u);
   slot = __shfl_sync(kFull, slot, 0);
@@ -310,9 +324,9 @@ static __device__ __noinline__ int refine_in_warp(const Batch& p, double un, dou
         if (nn < kIwBoxes) {
           const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
           if (lane < 27) {
-            const int i = lane % 3, jj = (lane / 3) % 3, k = lane / 9;
+            const int x = sx + lane % 3, y = sy + (lane / 3) % 3, z = sz + lane / 9;
             out[static_cast<uint64_t>(lane) * kIwBoxes + nn] =
-                G[(sx + i) + 5 * ((sy + jj) + 5 * (sz + k))];
+                down2(G[x + 5 * (y + 5 * z)], split_exp3(x, y, z));
           }
         } else {
           bits |= kStOverflow;
@@ -449,35 +463,37 @@ static __device__ __noinline__ void refine_box_warp(const Batch& p, int level, u
   double* P2 = sm + 72;    // [i + 5 (j + 5 k)], i, j < 5
   double* G = sm + 147;    // [i + 5 (j + 5 k)], i, j, k < 5
   if (lane < 27) A[lane] = ldcg(S.qcoef[in] + static_cast<uint64_t>(lane) * S.qcap + idx);
-  const double E = fma(static_cast<double>(child_level) * 0x1p-49, ldcg(S.slot_m0 + slot),
-                       ldcg(S.slot_e0 + slot));
+  const double m0 = ldcg(S.slot_m0 + slot);
+  const double E = fma(static_cast<double>(child_level) * 0x1p-49, m0, ldcg(S.slot_e0 + slot));
   const uint32_t key = dhi(E);
+  // unscaled split (hexval_internal.cuh): value (x, y, z) carries 2^split_exp3(x, y, z)
   __syncwarp();
   if (lane < 9) {  // along xi: row (j, k)
     int j = lane % 3, k = lane / 3;
-    split5_row(A + 3 * j + 9 * k, 1, P1 + 5 * (j + 3 * k), 1);
+    split5u_row(A + 3 * j + 9 * k, 1, P1 + 5 * (j + 3 * k), 1);
   }
   __syncwarp();
   if (lane < 15) {  // along eta: row (i, k)
     int i = lane % 5, k = lane / 5;
-    split5_row(P1 + i + 15 * k, 5, P2 + i + 25 * k, 5);
+    split5u_row(P1 + i + 15 * k, 5, P2 + i + 25 * k, 5);
   }
   __syncwarp();
   if (lane < 25) {  // along zeta: row (i, j)
     int i = lane % 5, j = lane / 5;
-    split5_row(P2 + i + 5 * j, 25, G + i + 5 * j, 25);
+    split5u_row(P2 + i + 5 * j, 25, G + i + 5 * j, 25);
   }
   __syncwarp();
   // lane o < 8 classifies child o
-  uint32_t bits = 0;
+  uint32_t bits = split_range_ok(m0) ? 0u : kStAmbig;  // else the exact tier decides
   bool want = false, xwant = false;
-  if (lane < 8) {
+  if (lane < 8 && !bits) {
     const int sx = 2 * (lane & 1), sy = 2 * ((lane >> 1) & 1), sz = 2 * (lane >> 2);
     bool nonpos = false, amb = false, notcert = false, amb2 = false;
     for (int k = 0; k < 3; ++k)
       for (int j = 0; j < 3; ++j)
         for (int i = 0; i < 3; ++i) {
-          Sign3 q = sign_d(G[(sx + i) + 5 * ((sy + j) + 5 * (sz + k))], key);
+          Sign3 q = sign_d_split(G[(sx + i) + 5 * ((sy + j) + 5 * (sz + k))],
+                                 key, split_exp3(sx + i, sy + j, sz + k));
           if ((i != 1) && (j != 1) && (k != 1)) {
             nonpos |= q.nonpos;
             amb |= !(q.nonpos | q.pos);
@@ -518,9 +534,9 @@ static __device__ __noinline__ void refine_box_warp(const Batch& p, int level, u
       if (pos < S.qcap) {
         const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
         if (lane < 27) {
-          int i = lane % 3, j = (lane / 3) % 3, k = lane / 9;
+          const int x = sx + lane % 3, y = sy + (lane / 3) % 3, z = sz + lane / 9;
           S.qcoef[out][static_cast<uint64_t>(lane) * S.qcap + pos] =
-              G[(sx + i) + 5 * ((sy + j) + 5 * (sz + k))];
+              down2(G[x + 5 * (y + 5 * z)], split_exp3(x, y, z));
         }
         if (lane == 0) {
           S.qslot[out][pos] = slot;
