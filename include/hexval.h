@@ -217,6 +217,24 @@ int hexval_check_indexed(hexval_handle h, int64_t n_nodes, const double* nodes, 
                          const int32_t* conn, uint8_t* flags, double* bmin, double* bmax,
                          void* stream);
 
+/* The same check in two steps, for many calls on one node array (an indexed
+ * mesh checked in ranges of elements whose copies overlap the checks, or
+ * candidate element sets sharing one node array): hexval_prepare_nodes
+ * records the node array on the handle and, with HEXVAL_FP32_FILTERED,
+ * enqueues its conversion to the handle's FP32 node records (once);
+ * hexval_check_indexed_prepared then checks n_hex elements (conn as in
+ * hexval_check_indexed, any range of the mesh's rows) against it, without
+ * converting the nodes again.  Results are those of hexval_check_indexed on
+ * the same nodes and rows.  Not from the paper: a data-movement step of
+ * this library.  The caller keeps the node array unchanged and orders the
+ * prepare call before the checks (same stream, or an event); a later
+ * hexval_check_indexed on the handle replaces the FP32 node records, after
+ * which hexval_check_indexed_prepared returns HEXVAL_E_ARG until the next
+ * prepare.  Argument rules as hexval_check_indexed. */
+int hexval_prepare_nodes(hexval_handle h, int64_t n_nodes, const double* nodes, void* stream);
+int hexval_check_indexed_prepared(hexval_handle h, int64_t n_hex, const int32_t* conn,
+                                  uint8_t* flags, double* bmin, double* bmax, void* stream);
+
 /* Validity of linear quadrangles (Sec. 2.1, Eq. e:determinant2D): the
  * Jacobian determinant of the bilinear map is bilinear, so the element is
  * valid iff its values at the four corners are all positive (strictly).

@@ -68,6 +68,10 @@ struct hexval_ctx {
   uint64_t scratch_bytes = 0;  // device bytes allocated by hexval_create
   Profiler prof;
   Replay replay;
+  // node array recorded by hexval_prepare_nodes (its FP32 records in s.node32
+  // with the FP32 form); cleared by hexval_check_indexed
+  const double* prep_nodes = nullptr;
+  int64_t prep_n = 0;
 };
 
 namespace {
@@ -175,7 +179,8 @@ int run_batches(hexval_ctx* h, Batch p, int64_t n_hex, cudaStream_t st) {
   return HEXVAL_OK;
 }
 
-// The launch sequence of one check call.
+// The launch sequence of one check call (kind 0 SoA, 1 indexed, 2 indexed on
+// prepared nodes: no node conversion).
 int launch_call(hexval_ctx* h, const Batch& p, int kind, int64_t n_hex, cudaStream_t st) {
   if (kind == 1 && h->cfg.precision == HEXVAL_FP32_FILTERED &&
       phase(h, HEXVAL_PH_NODES32, st, [&] { return hexval::launch_nodes32(p, st); }) !=
@@ -221,7 +226,8 @@ bool capture_call(hexval_ctx* h, const Batch& p, int kind, int64_t n_hex) {
 
 // Direct launches, or the replay of a repeated call.
 int run_call(hexval_ctx* h, const Batch& p, int kind, int64_t n_hex, cudaStream_t st) {
-  NvtxRange range(kind ? "hexval_check_indexed" : "hexval_check_soa");
+  NvtxRange range(kind == 0 ? "hexval_check_soa"
+                            : kind == 1 ? "hexval_check_indexed" : "hexval_check_indexed_prepared");
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if ((h->cfg.options & HEXVAL_OPT_NO_REPLAY) || h->prof.on ||
       cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
@@ -242,6 +248,30 @@ int run_call(hexval_ctx* h, const Batch& p, int kind, int64_t n_hex, cudaStream_
   if (!repeat || !capture_call(h, p, kind, n_hex)) return launch_call(h, p, kind, n_hex, st);
   std::memcpy(&R.cached, &k, sizeof(k));
   return cudaGraphLaunch(R.exec, st) == cudaSuccess ? HEXVAL_OK : HEXVAL_E_CUDA;
+}
+
+// Batch of an indexed check on nodes (n_nodes) and rows conn.
+Batch indexed_batch(const hexval_ctx* h, int64_t n_nodes, const double* nodes,
+                    const int32_t* conn, uint8_t* flags, double* bmin, double* bmax) {
+  Batch p{};
+  p.nodes = nodes;
+  p.n_nodes = n_nodes;
+  p.conn = conn;
+  p.indexed = 1;
+  p.pair32 = (h->cfg.options & HEXVAL_OPT_PAIR32) != 0;
+  p.prefetch32 = (h->cfg.options & HEXVAL_OPT_PREFETCH) != 0;
+  p.dfredo = (h->cfg.options & HEXVAL_OPT_DFREDO) != 0;
+  p.level1 = (h->cfg.options & HEXVAL_OPT_LEVEL1) != 0;
+  p.bulk_threads = static_cast<int>(h->cfg.bulk_threads);
+  p.esc_in_pass = h->cfg.esc_in_pass;
+  p.r32_in_pass = h->cfg.refine_in_pass;
+  p.warp_items = h->cfg.tail_warp_items;
+  p.flags = flags;
+  p.bmin = bmin;
+  p.bmax = bmax;
+  p.max_depth = h->cfg.max_depth;
+  p.s = h->s;
+  return p;
 }
 
 }  // namespace
@@ -385,26 +415,40 @@ int hexval_check_indexed(hexval_handle h, int64_t n_nodes, const double* nodes, 
   if (h->cfg.precision == HEXVAL_FP32_FILTERED && static_cast<uint64_t>(n_nodes) > h->s.max_nodes)
     return HEXVAL_E_ARG;
   if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Batch p{};
-  p.nodes = nodes;
-  p.n_nodes = n_nodes;
-  p.conn = conn;
-  p.indexed = 1;
-  p.pair32 = (h->cfg.options & HEXVAL_OPT_PAIR32) != 0;
-  p.prefetch32 = (h->cfg.options & HEXVAL_OPT_PREFETCH) != 0;
-  p.dfredo = (h->cfg.options & HEXVAL_OPT_DFREDO) != 0;
-  p.level1 = (h->cfg.options & HEXVAL_OPT_LEVEL1) != 0;
-  p.bulk_threads = static_cast<int>(h->cfg.bulk_threads);
-  p.esc_in_pass = h->cfg.esc_in_pass;
-  p.r32_in_pass = h->cfg.refine_in_pass;
-  p.warp_items = h->cfg.tail_warp_items;
-  p.flags = flags;
-  p.bmin = bmin;
-  p.bmax = bmax;
-  p.max_depth = h->cfg.max_depth;
-  p.s = h->s;
-  return run_call(h, p, 1, n_hex, st);
+  h->prep_nodes = nullptr;  // the FP32 node records are replaced
+  h->prep_n = 0;
+  return run_call(h, indexed_batch(h, n_nodes, nodes, conn, flags, bmin, bmax), 1, n_hex,
+                  static_cast<cudaStream_t>(stream));
+}
+
+int hexval_prepare_nodes(hexval_handle h, int64_t n_nodes, const double* nodes, void* stream) {
+  if (!h || !nodes || n_nodes <= 0 || n_nodes >= (1ll << 31)) return HEXVAL_E_ARG;
+  if (h->cfg.precision == HEXVAL_FP32_FILTERED && static_cast<uint64_t>(n_nodes) > h->s.max_nodes)
+    return HEXVAL_E_ARG;
+  if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;
+  h->prep_nodes = nullptr;
+  h->prep_n = 0;
+  if (h->cfg.precision == HEXVAL_FP32_FILTERED) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Batch p = indexed_batch(h, n_nodes, nodes, nullptr, nullptr, nullptr, nullptr);
+    if (phase(h, HEXVAL_PH_NODES32, st, [&] { return hexval::launch_nodes32(p, st); }) !=
+        cudaSuccess)
+      return HEXVAL_E_CUDA;
+  }
+  h->prep_nodes = nodes;
+  h->prep_n = n_nodes;
+  return HEXVAL_OK;
+}
+
+int hexval_check_indexed_prepared(hexval_handle h, int64_t n_hex, const int32_t* conn,
+                                  uint8_t* flags, double* bmin, double* bmax, void* stream) {
+  if (!h || n_hex < 0 || n_hex >= (1ll << 31)) return HEXVAL_E_ARG;
+  if (n_hex == 0) return HEXVAL_OK;
+  if (!h->prep_nodes || !conn || !flags) return HEXVAL_E_ARG;
+  if (reinterpret_cast<uintptr_t>(conn) % 16 != 0) return HEXVAL_E_ARG;  // int4 rows
+  if (set_device(h) != HEXVAL_OK) return HEXVAL_E_CUDA;
+  return run_call(h, indexed_batch(h, h->prep_n, h->prep_nodes, conn, flags, bmin, bmax), 2,
+                  n_hex, static_cast<cudaStream_t>(stream));
 }
 
 int hexval_check_quads(hexval_handle h, int64_t n_quad, const double* corners, uint8_t* flags,

@@ -34,7 +34,7 @@ EXPORTS = ("hexval_config_default", "hexval_create", "hexval_destroy", "hexval_c
            "hexval_check_quads_indexed", "hexval_corner_quality",
            "hexval_corner_quality_indexed", "hexval_compact", "hexval_min_jacobian",
            "hexval_min_jacobian_indexed", "hexval_strerror", "hexval_scratch_bytes",
-           "hexval_copy_soa_range")
+           "hexval_copy_soa_range", "hexval_prepare_nodes", "hexval_check_indexed_prepared")
 PHASES = ("nodes32", "bulk32", "bulk64", "tail", "-", "redo_df", "level1", "-")
 
 
@@ -91,6 +91,8 @@ def load(build_if_missing=False):
     lib.hexval_destroy.argtypes = [vp]
     lib.hexval_check_soa.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     lib.hexval_check_indexed.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, vp]
+    lib.hexval_prepare_nodes.argtypes = [vp, i64, vp, vp]
+    lib.hexval_check_indexed_prepared.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     lib.hexval_status.argtypes = [vp, vp]
     lib.hexval_scratch_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     lib.hexval_copy_soa_range.argtypes = [vp, vp, i64, i64, i64, vp]
@@ -226,6 +228,33 @@ class Validator:
                                             self._ptr(conn), self._ptr(flags), self._ptr(bmin),
                                             self._ptr(bmax), _stream_ptr(stream))
         _check(rc, "hexval_check_indexed")
+        return flags, bmin, bmax
+
+    def prepare_nodes(self, nodes, stream=None):
+        """Records `nodes` (float64 CUDA (n_nodes, 3)) for check_indexed_prepared
+        and, in the FP32 form, converts them once.  The tensor must stay
+        alive and unchanged while it is used."""
+        import torch
+        if nodes.dtype != torch.float64 or not nodes.is_cuda or not nodes.is_contiguous() or \
+                nodes.dim() != 2 or nodes.shape[1] != 3:
+            raise ValueError("nodes must be a contiguous float64 CUDA tensor (n_nodes, 3)")
+        _check(self._lib.hexval_prepare_nodes(self._h, nodes.shape[0], self._ptr(nodes),
+                                              _stream_ptr(stream)), "hexval_prepare_nodes")
+        self._prepared = nodes  # kept alive with the handle's record of it
+
+    def check_indexed_prepared(self, conn, out=None, stream=None):
+        """check_indexed of rows conn (int32 CUDA (n, 8)) on the nodes of the
+        last prepare_nodes."""
+        import torch
+        if conn.dtype != torch.int32 or not conn.is_cuda or not conn.is_contiguous() or \
+                conn.dim() != 2 or conn.shape[1] != 8:
+            raise ValueError("conn must be a contiguous int32 CUDA tensor (n_hex, 8)")
+        n = conn.shape[0]
+        flags, bmin, bmax = self._outputs(n, out)
+        rc = self._lib.hexval_check_indexed_prepared(self._h, n, self._ptr(conn), self._ptr(flags),
+                                                     self._ptr(bmin), self._ptr(bmax),
+                                                     _stream_ptr(stream))
+        _check(rc, "hexval_check_indexed_prepared")
         return flags, bmin, bmax
 
     def check_quads(self, corners, out=None, stream=None):
@@ -364,7 +393,8 @@ class Validator:
         the current stream), device-to-host copies on a third; `stream` waits
         for the last copy, so an event recorded on it after this call marks
         the outputs as ready.  An indexed mesh copies all its nodes first
-        (every range may use any node)."""
+        (every range may use any node) and prepares them once
+        (prepare_nodes)."""
         import torch
         dev = self.device
         main = stream if stream is not None else torch.cuda.current_stream(dev)
@@ -390,6 +420,9 @@ class Validator:
                 conn = torch.empty(arrays[1].shape, dtype=arrays[1].dtype, device=dev)
                 nodes.record_stream(main)  # used by the checks on `main`
                 conn.record_stream(main)
+        if kind == "indexed":  # the nodes are converted once for all ranges
+            main.wait_stream(cin)
+            self.prepare_nodes(nodes, stream=main)
         for i in range(k):
             lo, hi = bounds[i], bounds[i + 1]
             if hi == lo:
@@ -404,7 +437,7 @@ class Validator:
             main.wait_stream(cin)
             o = tuple(t[lo:hi] for t in out)
             if kind == "indexed":
-                self.check_indexed(nodes, conn[lo:hi], out=o, stream=main)
+                self.check_indexed_prepared(conn[lo:hi], out=o, stream=main)
             else:
                 self.check_soa(X, out=o, stream=main)
             cout.wait_stream(main)

@@ -126,3 +126,12 @@ def test_copy_soa_range_refuses_bad_ranges(lib):
     assert lib.hexval_copy_soa_range(p, p, 10, 6, 5, None) == -1
     assert lib.hexval_copy_soa_range(p, p, 10, -1, 5, None) == -1
     assert lib.hexval_copy_soa_range(p, p, 10, 3, 0, None) == 0  # empty: nothing to do
+
+
+def test_prepared_nodes_refusals(lib):
+    """The prepared-node entry points check their arguments on the host: no
+    handle, no node array, or no prepared nodes is HEXVAL_E_ARG."""
+    buf = ctypes.create_string_buffer(64)
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    assert lib.hexval_prepare_nodes(None, 10, p, None) == -1
+    assert lib.hexval_check_indexed_prepared(None, 10, p, p, None, None, None) == -1

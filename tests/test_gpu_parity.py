@@ -658,6 +658,33 @@ def test_host_buffers_pipeline(kind, chunks):
     v.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_prepared_nodes_in_ranges(prec):
+    """hexval_prepare_nodes + hexval_check_indexed_prepared over ranges of
+    rows give hexval_check_indexed's outputs on the whole mesh, every bit; a
+    check_indexed on the handle drops the prepared nodes (E_ARG until the
+    next prepare)."""
+    nodes, conn = synth.structured_grid(40, 23, 19, sigma=0.35, seed=98)
+    N, C = torch.from_numpy(nodes).cuda(), torch.from_numpy(conn).cuda()
+    v = hv.Validator(precision=prec, max_depth=8, options=hv.OPT_NO_REPLAY, **CAPS)
+    want = [t.cpu().numpy() for t in v.check_indexed(N, C)]
+    v.prepare_nodes(N)
+    n = len(conn)
+    cuts = [0, 1, 777, n // 2, n - 5, n]
+    got = [np.empty_like(w) for w in want]
+    for lo, hi in zip(cuts[:-1], cuts[1:]):
+        part = v.check_indexed_prepared(C[lo:hi])
+        for g, t in zip(got, part):
+            g[lo:hi] = t.cpu().numpy()
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w)
+    assert v.status() == 0
+    v.check_indexed(N, C[:10])
+    with pytest.raises(hv.HexvalError):
+        v.check_indexed_prepared(C[:10])
+    v.close()
+
+
 def test_copy_soa_range_from_host_and_device():
     """One strided copy of an element range of SoA planes, from pinned host
     memory and from device memory, equals the slice."""
