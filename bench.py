@@ -47,11 +47,11 @@ FP64_PEAK = 1.25 / 2
 FP32_PEAK = 152 * 128 * 2.07e9 / 1e12
 # FP64 instructions of one hexahedron in the FP64 bulk pass, as ncu counts
 # them (DADD 132, DFMA 107, DMUL 103 per element on the 128^3 mesh:
-# profiles/bulk64_mesh128.txt), and of one box expansion (three de Casteljau
-# passes over 9, 15 and 25 rows, 6 operations a row; the same count in FP32
-# for an FP32 box)
+# profiles/bulk64_mesh128.txt), and of one box expansion (three unscaled de
+# Casteljau passes over 9, 15 and 25 rows, 3 additions a row; the same count
+# in FP32 for an FP32 box)
 OPS_PER_HEX = 366
-OPS_PER_BOX = 294
+OPS_PER_BOX = 147
 
 
 # ------------------------------------------------------------- workloads ----
@@ -226,7 +226,8 @@ def timed_steps(v, w, dev_in, steps, warmup, flush, profile=False):
 def e2e_steps(v, w, steps, warmup, chunks=4):
     """Public API on host data: pinned host inputs copied in and all three
     outputs (flags, bmin, bmax) copied out every step, the copies of each
-    chunk of elements overlapping the checks of the others."""
+    chunk of elements overlapping the checks of the others, the sequence
+    replayed from a CUDA graph (HostPipeline)."""
     import torch
     if w["kind"] == "indexed":
         host = (torch.from_numpy(w["nodes"]).pin_memory(), torch.from_numpy(w["conn"]).pin_memory())
@@ -234,14 +235,15 @@ def e2e_steps(v, w, steps, warmup, chunks=4):
         host = (torch.from_numpy(w["X"]).pin_memory(),)
     h2d = sum(t.numel() * t.element_size() for t in host)
     d2h = 17 * w["n"]
+    pipe = v.host_pipeline(w["kind"], *host, chunks=chunks)
     for _ in range(warmup):
-        v.check_host(w["kind"], *host, chunks=chunks)
+        pipe.run()
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record()
     for _ in range(steps):
-        res = v.check_host(w["kind"], *host, chunks=chunks)
+        res = pipe.run()
     t1.record()
     torch.cuda.synchronize()
     v.raise_on_status()
@@ -655,6 +657,34 @@ def config_summary(cfg, steps, warmup, flush, retune=False):
 
 # ------------------------------------------------------------------- main ---
 
+def profile_case(args, hv, torch):
+    """--case: three calls of one kernel sequence on the workload (--config,
+    --n), nothing timed, for profiler captures of committed code."""
+    w = workload(args.config, 0, n=args.n)
+    if w["kind"] == "indexed":
+        dev = (torch.from_numpy(w["nodes"]).cuda(), torch.from_numpy(w["conn"]).cuda())
+    else:
+        dev = (torch.from_numpy(w["X"]).cuda(),)
+    prec = "fp64" if args.case == "fp64" else "fp32"
+    v = hv.Validator(precision=prec, max_depth=w["depth"], options=args.options | hv.OPT_NO_REPLAY,
+                     **w.get("caps", {}))
+    for _ in range(3):
+        if args.case == "quality":
+            if w["kind"] == "indexed":
+                v.corner_quality_indexed(*dev)
+            else:
+                v.corner_quality(*dev)
+        elif w["kind"] == "indexed":
+            v.check_indexed(*dev)
+        else:
+            v.check_soa(*dev)
+    torch.cuda.synchronize()
+    v.raise_on_status()
+    print(json.dumps({"case": args.case, "workload": w["name"], "calls": 3}))
+    v.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -682,6 +712,10 @@ def main():
     ap.add_argument("--bulk-threads", type=int, default=None,
                     help="fixed FP32 launch configuration instead of the autotuner's")
     ap.add_argument("--options", type=int, default=0, help="options with --bulk-threads")
+    ap.add_argument("--case", choices=["quality", "fp32", "fp64"], default=None,
+                    help="profiler captures: run one kernel sequence on the workload three "
+                         "times and exit (corner quality, or a check in one form with "
+                         "--options)")
     ap.add_argument("--no-quads", dest="quads", action="store_false",
                     help="skip the quadrangle and candidate-filtering measurements")
     args = ap.parse_args()
@@ -707,6 +741,8 @@ def main():
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
+    if args.case:
+        return profile_case(args, hv, torch)
     if args.serve:
         from paper_1706_01613_gb300 import serve
         pool = serve.Pool(args.serve_max_n)

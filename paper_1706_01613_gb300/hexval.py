@@ -384,6 +384,10 @@ class Validator:
         _check(rc, "hexval_min_jacobian_indexed")
         return lo, hi, depth
 
+    def host_pipeline(self, kind, *arrays, chunks=4):
+        """A HostPipeline of this handle on pinned host inputs (see there)."""
+        return HostPipeline(self, kind, *arrays, chunks=chunks)
+
     def check_host(self, kind, *arrays, chunks=4, stream=None):
         """End-to-end call on host data: pinned host inputs in, pinned host
         outputs (flags, bmin, bmax) back.  kind = "soa" (corners) or
@@ -493,6 +497,97 @@ def copy_soa_range(dst, src, first, stream=None):
                                       _stream_ptr(stream))
     _check(rc, "hexval_copy_soa_range")
     return dst
+
+
+class HostPipeline:
+    """End-to-end checks of one set of pinned host inputs, replayed from a
+    CUDA graph.
+
+    Validator.check_host issues every copy, wait and check from Python on
+    each call; for a mesh checked again and again (its host buffers updated
+    in place between runs) that host-side issue cost can exceed the copies.
+    Here the whole sequence -- host-to-device copies of `chunks` element
+    ranges on one stream, the checks of each range on a second as soon as
+    its copy is done (indexed: the nodes first, prepared once), the
+    device-to-host copies of flags, bmin and bmax on a third -- is recorded
+    once into a CUDA graph; run() replays it, one launch.  Every run copies
+    the current contents of the input buffers and overwrites the host
+    outputs.  Device and host buffers are allocated here, once."""
+
+    def __init__(self, validator, kind, *arrays, chunks=4):
+        import torch
+        if kind not in ("soa", "indexed"):
+            raise ValueError("kind: soa or indexed")
+        for a in arrays:
+            if a.is_cuda or not a.is_pinned() or not a.is_contiguous():
+                raise ValueError("inputs must be contiguous pinned host tensors")
+        self.v, self.kind, self.arrays = validator, kind, arrays
+        dev = validator.device
+        n = arrays[0].shape[2] if kind == "soa" else arrays[1].shape[0]
+        self.n = n
+        k = max(1, min(int(chunks), n))
+        self.bounds = [n * i // k for i in range(k + 1)]
+        self.host = (torch.empty(n, dtype=torch.uint8, pin_memory=True),
+                     torch.empty(n, dtype=torch.float64, pin_memory=True),
+                     torch.empty(n, dtype=torch.float64, pin_memory=True))
+        self.dev_out = (torch.empty(n, dtype=torch.uint8, device=dev),
+                        torch.empty(n, dtype=torch.float64, device=dev),
+                        torch.empty(n, dtype=torch.float64, device=dev))
+        if kind == "indexed":
+            self.nodes = torch.empty(arrays[0].shape, dtype=arrays[0].dtype, device=dev)
+            self.conn = torch.empty(arrays[1].shape, dtype=arrays[1].dtype, device=dev)
+        else:
+            self.X = [torch.empty((8, 3, hi - lo), dtype=arrays[0].dtype, device=dev)
+                      for lo, hi in zip(self.bounds[:-1], self.bounds[1:])]
+        self.streams = (torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev))
+        main = self.streams[0]
+        main.wait_stream(torch.cuda.current_stream(dev))
+        self._enqueue()  # once directly first: lazy initialisation stays out of the capture
+        main.synchronize()
+        validator.raise_on_status()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=main):
+            self._enqueue()
+
+    def _enqueue(self):
+        import torch
+        main, cin, cout = self.streams
+        v = self.v
+        cin.wait_stream(main)
+        if self.kind == "indexed":
+            with torch.cuda.stream(cin):
+                self.nodes.copy_(self.arrays[0], non_blocking=True)
+            main.wait_stream(cin)
+            v.prepare_nodes(self.nodes, stream=main)
+        for i, (lo, hi) in enumerate(zip(self.bounds[:-1], self.bounds[1:])):
+            if hi == lo:
+                continue
+            with torch.cuda.stream(cin):
+                if self.kind == "indexed":
+                    self.conn[lo:hi].copy_(self.arrays[1][lo:hi], non_blocking=True)
+                else:
+                    copy_soa_range(self.X[i], self.arrays[0], lo, stream=cin)
+            main.wait_stream(cin)
+            o = tuple(t[lo:hi] for t in self.dev_out)
+            if self.kind == "indexed":
+                v.check_indexed_prepared(self.conn[lo:hi], out=o, stream=main)
+            else:
+                v.check_soa(self.X[i], out=o, stream=main)
+            cout.wait_stream(main)
+            with torch.cuda.stream(cout):
+                for h, d in zip(self.host, o):
+                    h[lo:hi].copy_(d, non_blocking=True)
+        main.wait_stream(cout)
+
+    def run(self, stream=None):
+        """Replays the pipeline on `stream` (default: the current stream) and
+        returns the pinned host outputs (flags, bmin, bmax), valid once the
+        stream reaches this point."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.v.device)
+        with torch.cuda.stream(s):
+            self.graph.replay()
+        return self.host
 
 
 NOALLOC_MAX_HEX = 16384

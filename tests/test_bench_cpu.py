@@ -57,7 +57,7 @@ def test_roofline_of_each_dominant_kernel(bench):
     roof, _ = bench.roofline_of(w, {"bulk32": (0.1, 1), "tail": (20.0, 10)}, stats, 10)
     assert roof["kernel"] == "tail" and roof["pipe"] == "fp64"
     assert roof["box_expansions_per_call"] == {"fp64": 200_000.0, "fp32": 100_000.0}
-    assert abs(roof["fp64_frac"] - 294 * 200_000 / 2e-3 / 1e12 / 0.625) < 1e-9
+    assert abs(roof["fp64_frac"] - 147 * 200_000 / 2e-3 / 1e12 / 0.625) < 1e-9
     roof, _ = bench.roofline_of(w, {"bulk32": (0.1, 1), "tail": (2.0, 10)}, {}, 10)
     assert roof["bound"] == "latency"
     roof, _ = bench.roofline_of(w, {"bulk32": (0.1, 1), "tail": (2.0, 10)},

@@ -658,6 +658,44 @@ def test_host_buffers_pipeline(kind, chunks):
     v.close()
 
 
+@pytest.mark.parametrize("kind", ["indexed", "soa"])
+def test_host_pipeline_graph_replay(kind):
+    """HostPipeline (the chunked host call recorded into a CUDA graph): each
+    run gives the device-resident call's verdicts on the current contents of
+    the pinned inputs (changed in place between runs), with bounds within
+    each element's certified bound."""
+    v = hv.Validator(precision="fp32", max_depth=8, **CAPS)
+    if kind == "indexed":
+        nodes, conn = synth.structured_grid(30, 21, 17, sigma=0.3, seed=99)
+        host = (torch.from_numpy(nodes).pin_memory(), torch.from_numpy(conn).pin_memory())
+    else:
+        X = synth.perturbed_cubes(10_007, noise=0.45, seed=100)
+        host = (torch.from_numpy(X).pin_memory(),)
+    pipe = v.host_pipeline(kind, *host, chunks=3)
+    for step in range(2):
+        if step == 1:  # new contents in the same pinned buffers
+            if kind == "indexed":
+                host[0][::7] *= 1.01
+                host[0][5::11] += 0.2
+            else:
+                host[0][:, :, ::5] = host[0][:, :, ::5].flip(0)  # reversed node order: inverted
+        res = pipe.run()
+        torch.cuda.synchronize()  # the host outputs are written by the replay
+        got = [t.numpy().copy() for t in res]
+        if kind == "indexed":
+            a, c = host[0].numpy(), host[1].numpy()
+            want = [t.cpu().numpy() for t in v.check_indexed(host[0].cuda(), host[1].cuda())]
+            oracle_out, Xs = oracle.check_indexed(a, c, max_depth=8), _soa(a, c)
+        else:
+            Xs = host[0].numpy()
+            want = [t.cpu().numpy() for t in v.check_soa(host[0].cuda())]
+            oracle_out = oracle.check_soa(Xs, max_depth=8)
+        assert np.array_equal(got[0] & 0x7F, want[0] & 0x7F)
+        _compare("fp32", got, oracle_out, Xs)
+    assert v.status() == 0
+    v.close()
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_prepared_nodes_in_ranges(prec):
     """hexval_prepare_nodes + hexval_check_indexed_prepared over ranges of
