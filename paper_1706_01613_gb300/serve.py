@@ -59,9 +59,15 @@ class Request:
 
 
 class Scheduler:
-    """FIFO admission under a slot count and a byte budget."""
+    """FIFO admission under a slot count and a byte budget.  The first
+    `small_slots` slots take only requests of at most `small_n` elements, so
+    that a short request arriving while long ones hold the other slots
+    starts at once instead of waiting behind them (it may pass requests that
+    wait for a general slot; among those the order stays FIFO)."""
 
-    def __init__(self, slots, budget_bytes, reserved_bytes=0):
+    def __init__(self, slots, budget_bytes, reserved_bytes=0, small_slots=0, small_n=0):
+        self.small = set(range(min(small_slots, max(0, slots - 1))))  # a general slot is kept
+        self.small_n = int(small_n)
         self.free_slots = list(range(slots))
         self.budget = int(budget_bytes) - int(reserved_bytes)  # left for requests
         self.in_use = 0
@@ -74,30 +80,62 @@ class Scheduler:
         else:
             self.pending.append(req)
 
+    def _take(self, small_ok):
+        for i, s in enumerate(self.free_slots):
+            if s not in self.small:
+                return self.free_slots.pop(i)
+        if small_ok:
+            for i, s in enumerate(self.free_slots):
+                if s in self.small:
+                    return self.free_slots.pop(i)
+        return None
+
     def admissible(self):
         """Pops and returns (slot, request) pairs that can start now."""
         out = []
-        while self.pending and self.free_slots:
-            req = self.pending[0]
-            if self.in_use + req.bytes > self.budget:
-                break
-            self.pending.popleft()
-            slot = self.free_slots.pop()
+        kept = collections.deque()
+        general_blocked = False  # an earlier request waits for a general slot
+        while self.pending:
+            req = self.pending.popleft()
+            small_ok = bool(self.small) and req.n <= self.small_n
+            slot = None
+            if self.in_use + req.bytes <= self.budget:
+                if not general_blocked:
+                    slot = self._take(small_ok)
+                elif small_ok:
+                    slot = self._take_small()
+            if slot is None:
+                kept.append(req)
+                general_blocked = True
+                if not self.small:
+                    break  # plain FIFO: nothing behind the head may start
+                continue
             self.in_use += req.bytes
             out.append((slot, req))
+        kept.extend(self.pending)
+        self.pending = kept
         return out
+
+    def _take_small(self):
+        for i, s in enumerate(self.free_slots):
+            if s in self.small:
+                return self.free_slots.pop(i)
+        return None
 
     def release(self, slot, req):
         self.in_use -= req.bytes
         self.free_slots.append(slot)
 
 
-def run_stream(requests, executor, slots, budget_bytes, now=time.perf_counter, idle=None):
+def run_stream(requests, executor, slots, budget_bytes, now=time.perf_counter, idle=None,
+               small_slots=0, small_n=0):
     """Serves `requests` (sorted by arrival, times in seconds from the start)
     on `executor`; returns the scheduler (for the rejected list).  The
     executor's fixed device memory (`fixed_bytes`, the slots' scratch) is
-    charged to the budget before any request."""
-    sched = Scheduler(slots, budget_bytes, getattr(executor, "fixed_bytes", 0))
+    charged to the budget before any request; `small_slots` slots are kept
+    for requests of at most `small_n` elements."""
+    sched = Scheduler(slots, budget_bytes, getattr(executor, "fixed_bytes", 0), small_slots,
+                      small_n)
     order = sorted(requests, key=lambda r: r.arrival)
     t0 = now()
     executor.start()

@@ -127,3 +127,22 @@ def test_pool_requests_are_cut_lazily():
     assert r.bytes == (192 + 17) * 7
     got = r.host_arrays()[0]
     assert got.is_contiguous() and torch.equal(got, X[:, :, 11:18])
+
+
+def test_short_requests_pass_long_ones_on_their_slot():
+    """With one of three slots kept for requests of at most 1000 elements, a
+    short request arriving while two long ones run and a third waits starts
+    at once on that slot; long requests never take it and keep FIFO order."""
+    clk = Clock()
+    ex = FakeExecutor(clk, lambda r: 1.0 if r.n > 1000 else 0.01)
+    reqs = [serve.Request(i, "soa", (FakeArray(10),), n, a)
+            for i, (n, a) in enumerate([(5000, 0.0), (5000, 0.0), (5000, 0.0), (50, 0.1),
+                                        (5000, 0.2)])]
+    serve.run_stream(reqs, ex, slots=3, budget_bytes=1 << 30, now=clk.now, idle=clk.tick,
+                     small_slots=1, small_n=1000)
+    starts = {e[1]: (e[2], e[3]) for e in ex.log if e[0] == "start"}
+    assert starts[3][0] == 0 and starts[3][1] < 0.12  # the kept slot, at once
+    assert all(starts[i][0] != 0 for i in (0, 1, 2, 4))
+    order = [e[1] for e in ex.log if e[0] == "start"]
+    assert order.index(2) < order.index(4)  # FIFO among the long ones
+    assert reqs[3].done < reqs[0].done
