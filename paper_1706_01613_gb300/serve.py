@@ -202,6 +202,10 @@ class GpuExecutor:
         self.fixed_bytes = sum(v.scratch_bytes() for v in self.v)
         self.events = [None] * slots
         self.buffers = [None] * slots
+        # without kept results each slot copies its outputs into one pinned
+        # host buffer of its own, grown to the largest request it has run,
+        # instead of new pinned memory per request
+        self.host_out = [None] * slots
         self.t0 = None
 
     def start(self):
@@ -233,13 +237,27 @@ class GpuExecutor:
                 self.v[slot].check_soa(dev[0], out=out, stream=s)
             else:
                 self.v[slot].check_indexed(dev[0], dev[1], out=out, stream=s)
-            host = tuple(torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in out)
+            host = self._host_outputs(slot, req.n)
             for h, d in zip(host, out):
                 h.copy_(d, non_blocking=True)
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(s)
         self.events[slot] = ev
         self.buffers[slot] = (dev, out, host)
+
+    def _host_outputs(self, slot, n):
+        torch = self.torch
+        if self.keep_results:
+            return (torch.empty(n, dtype=torch.uint8, pin_memory=True),
+                    torch.empty(n, dtype=torch.float64, pin_memory=True),
+                    torch.empty(n, dtype=torch.float64, pin_memory=True))
+        buf = self.host_out[slot]
+        if buf is None or buf[0].shape[0] < n:  # the slot's previous request is done
+            buf = (torch.empty(n, dtype=torch.uint8, pin_memory=True),
+                   torch.empty(n, dtype=torch.float64, pin_memory=True),
+                   torch.empty(n, dtype=torch.float64, pin_memory=True))
+            self.host_out[slot] = buf
+        return tuple(t[:n] for t in buf)
 
     def poll(self, slot):
         return self.events[slot].query()
