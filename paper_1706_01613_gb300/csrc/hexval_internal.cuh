@@ -472,48 +472,39 @@ __device__ __forceinline__ float pow2f(int p) {
 // of 6 operations.  The scalings being exact, every unscaled entry is exactly
 // 2^c times the halved one (no overflow: |p| <= M keeps every entry of a
 // box's three passes within 64 M).  After the three passes entry
-// (x, y, z) of the 5x5x5 grid carries 2^(c(x)+c(y)+c(z)), which the sign
-// tests take into account (sign_*_split) and the children are stored
-// without (down2 / down2f).
+// (x, y, z) of the 5x5x5 grid carries 2^(c(x)+c(y)+c(z)).  The FP64
+// refinement takes the factor into its sign tests (sign_d_split) and removes
+// it from the children it stores by exponent arithmetic (down2): no FP64
+// instruction for either.  The FP32 refinement multiplies the 125 values by
+// 2^-m (split_box32, refine32.cuh): FP32 multiplies are cheap, and the
+// child classification then needs only two minima per child.
 __host__ __device__ constexpr int split_exp(int x) { return x < 2 ? x : 4 - x; }
 __host__ __device__ constexpr int split_exp3(int x, int y, int z) {
   return split_exp(x) + split_exp(y) + split_exp(z);
 }
 
-// sign_d / sign_f of the value 2^-m v against the key of E, v carrying the
-// factor 2^m: the magnitude's exponent field less m, compared as a signed
-// integer (a magnitude below 2^m is never certain).  The same test as
-// sign_*(2^-m v, key) for a normal 2^-m v; for a subnormal one it is as
+// sign_d of the value 2^-m v against the key of E, v carrying the factor
+// 2^m: the magnitude's exponent field less m, compared as a signed integer
+// (a magnitude below 2^m is never certain).  The same test as
+// sign_d(2^-m v, key) for a normal 2^-m v; for a subnormal one it is as
 // conservative (its magnitude is below every normal E).  Needs key + (m <<
-// 20) (FP32: m << 23) < 2^31, which the range of M0 the split runs in
-// (split_range_ok, E <= M0) guarantees.
+// 20) < 2^31, which the range of M0 the split runs in (split_range_ok,
+// E <= M0) guarantees.
 __device__ __forceinline__ Sign3 sign_d_split(double v, uint32_t ekey, int m) {
   const uint32_t h = dhi(v);
   const bool big = static_cast<int>((h & 0x7fffffffu) - (static_cast<uint32_t>(m) << 20)) >
                    static_cast<int>(ekey);
   return {big && (h >> 31), big && !(h >> 31)};
 }
-__device__ __forceinline__ Sign3 sign_f_split(float v, uint32_t ekey, int m) {
-  const uint32_t h = fbits(v);
-  const bool big = static_cast<int>((h & 0x7fffffffu) - (static_cast<uint32_t>(m) << 23)) >
-                   static_cast<int>(ekey);
-  return {big && (h >> 31), big && !(h >> 31)};
-}
 
 // 2^-m u for 0 <= m <= 6 by exponent arithmetic on the integer pipe: exact
 // when the result is normal; a result below the normal range becomes a zero
-// of u's sign (absolute error < 2^-1022, FP32: < 2^-126).
+// of u's sign (absolute error < 2^-1022).
 __device__ __forceinline__ double down2(double u, int m) {
   const long long b = __double_as_longlong(u);
   const uint32_t e = (static_cast<uint32_t>(b >> 32) >> 20) & 0x7ffu;
   return __longlong_as_double(e > static_cast<uint32_t>(m) ? b - (static_cast<long long>(m) << 52)
                                                            : b & (1LL << 63));
-}
-__device__ __forceinline__ float down2f(float u, int m) {
-  const uint32_t b = __float_as_uint(u);
-  const uint32_t e = (b >> 23) & 0xffu;
-  return __uint_as_float(e > static_cast<uint32_t>(m) ? b - (static_cast<uint32_t>(m) << 23)
-                                                      : b & 0x80000000u);
 }
 
 // Range of the root magnitude bound M0 in which the unscaled split runs; a

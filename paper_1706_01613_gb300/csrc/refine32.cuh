@@ -3,9 +3,10 @@
 // certainly non-positive) are refined breadth first with FP32 boxes, exactly
 // as the FP64 refinement of tail.cu (Sec. 6: split at 1/2 along xi, eta,
 // zeta by quadratic de Casteljau, computed unscaled as hexval_internal.cuh
-// describes; a child with a corner certainly <= 0 makes
-// the element INVALID at that level, a child with all 27 certainly > 0 is
-// certified, any other child is queued, or the depth cap is reached).
+// describes and then normalised, split_box32; a child with a corner
+// certainly <= 0 makes the element INVALID at that level, a child with all
+// 27 certainly > 0 is certified, any other child is queued, or the depth
+// cap is reached).
 // An element whose boxes meet a sign that the FP32 bound cannot settle, or
 // a full queue, is listed in esc2 and redone from scratch in FP64.
 //
@@ -29,25 +30,12 @@ __device__ __forceinline__ void split5uf(float p0, float p1, float p2, float q[5
   q[4] = p2;
 }
 
-// The first level of the FP32 refinement of one element, by one thread
-// (level1_kernel, HEXVAL_OPT_LEVEL1): its root box (the 27 depth-0
-// coefficients s in tensor order, as root32 stores them, M0 = max(|lo|,
-// |hi|) + E0 as root32 forms it) is split exactly as refine_box32 splits a
-// level-0 box, with the same bound E0 + 2^-20 M0 and the same
-// classification of the 8 children.  Returns the flag byte when level 1
-// decides the element -- a child corner certainly <= 0 (INVALID@1), all
-// children certified (VALID@1), or uncertified children at a depth cap of 1
-// (UNDECIDED) -- and -1 when it needs deeper levels or meets a sign FP32
-// cannot settle; the element then goes on to the tail's FP32 refinement,
-// which reaches the same verdict from the same root box.
-__device__ __forceinline__ int refine1_fp32(const Scaled<float>& s, float E0, float lo, float hi,
-                                            int max_depth) {
-  float A[27];
-  store_tensor(s, A);
-  const float M0 = fmaxf(fabsf(lo), fabsf(hi)) + E0;
-  if (!split_range_ok(M0)) return -1;  // the tail sends it to FP64
-  const float E = fmaf(0x1p-20f, M0, E0);
-  const uint32_t key = fbits(E);
+// The three unscaled de Casteljau passes of a box whose 27 coefficients are
+// A (tensor order) into G, then every value multiplied by 2^-split_exp3: G
+// holds the 125 values of the halving split (the multiplications are exact
+// but for a result below the normal range, rounded or flushed by less than
+// 2^-126, which the per-level slack covers inside split_range_ok's range).
+__device__ __forceinline__ void split_box32(const float A[27], float G[5][5][5]) {
   float P1[5][3][3];
 #pragma unroll
   for (int k = 0; k < 3; ++k)
@@ -68,32 +56,76 @@ __device__ __forceinline__ int refine1_fp32(const Scaled<float>& s, float E0, fl
 #pragma unroll
       for (int j = 0; j < 5; ++j) P2[i][j][k] = q[j];
     }
-  float G[5][5][5];
 #pragma unroll
   for (int j = 0; j < 5; ++j)
 #pragma unroll
     for (int i = 0; i < 5; ++i) split5uf(P2[i][j][0], P2[i][j][1], P2[i][j][2], G[i][j]);
+#pragma unroll
+  for (int x = 0; x < 5; ++x)
+#pragma unroll
+    for (int y = 0; y < 5; ++y)
+#pragma unroll
+      for (int z = 0; z < 5; ++z) {
+        const int m = split_exp3(x, y, z);
+        if (m) G[x][y][z] *= 1.f / static_cast<float>(1 << m);
+      }
+}
+
+// Classes of child (sx, sy, sz) of a box split by split_box32 against the
+// bound E, from the minimum of its 8 corner coefficients and of its 19
+// others: a corner certainly <= 0 (min < -E), a corner whose sign E cannot
+// settle (else min <= E), another coefficient certainly <= 0, another
+// unsettled -- the sign tests of Sec. 6's child decision, each class
+// needing only the smallest value of its set (the last two matter only
+// without the one before).
+struct Child32 {
+  bool nonpos, amb, notcert, amb2;
+};
+__device__ __forceinline__ Child32 classify_child32(const float G[5][5][5], int sx, int sy,
+                                                    int sz, float E) {
+  float c[8], o[19];
+  int nc = 0, no = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float v = G[sx + i][sy + j][sz + k];
+        if ((i != 1) && (j != 1) && (k != 1))
+          c[nc++] = v;
+        else
+          o[no++] = v;
+      }
+  const float mc = min_of<8>(c), mo = min_of<19>(o);
+  return {mc < -E, mc <= E, mo < -E, mo <= E};
+}
+
+// The first level of the FP32 refinement of one element, by one thread
+// (level1_kernel, HEXVAL_OPT_LEVEL1): its root box (the 27 depth-0
+// coefficients s in tensor order, as root32 stores them, M0 = max(|lo|,
+// |hi|) + E0 as root32 forms it) is split exactly as refine_box32 splits a
+// level-0 box, with the same bound E0 + 2^-20 M0 and the same
+// classification of the 8 children.  Returns the flag byte when level 1
+// decides the element -- a child corner certainly <= 0 (INVALID@1), all
+// children certified (VALID@1), or uncertified children at a depth cap of 1
+// (UNDECIDED) -- and -1 when it needs deeper levels or meets a sign FP32
+// cannot settle; the element then goes on to the tail's FP32 refinement,
+// which reaches the same verdict from the same root box.
+__device__ __forceinline__ int refine1_fp32(const Scaled<float>& s, float E0, float lo, float hi,
+                                            int max_depth) {
+  float A[27];
+  store_tensor(s, A);
+  const float M0 = fmaxf(fabsf(lo), fabsf(hi)) + E0;
+  if (!split_range_ok(M0)) return -1;  // the tail sends it to FP64
+  const float E = fmaf(0x1p-20f, M0, E0);
+  float G[5][5][5];
+  split_box32(A, G);
   bool invalid = false, open = false, capped = false;
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
-    const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
-    bool nonpos = false, amb = false, notcert = false, amb2 = false;
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const Sign3 q = sign_f_split(G[sx + i][sy + j][sz + k],
-                                       key, split_exp3(sx + i, sy + j, sz + k));
-          if ((i != 1) && (j != 1) && (k != 1)) {
-            nonpos |= q.nonpos;
-            amb |= !(q.nonpos | q.pos);
-          } else {
-            notcert |= q.nonpos;
-            amb2 |= !(q.nonpos | q.pos);
-          }
-        }
+    const Child32 q = classify_child32(G, 2 * (o & 1), 2 * ((o >> 1) & 1), 2 * (o >> 2), E);
+    const bool nonpos = q.nonpos, amb = q.amb, notcert = q.notcert, amb2 = q.amb2;
     if (nonpos) {
       invalid = true;
     } else if (amb) {
@@ -165,8 +197,8 @@ __device__ __forceinline__ void refine_box32(const Batch& p, int level, bool act
     if (m && (threadIdx.x & 31u) == static_cast<unsigned int>(__ffs(m) - 1))
       atomicAdd(&S.cnt->split32, static_cast<unsigned int>(__popc(m)));
   }
-  float G[5][5][5];  // unscaled: entry (x, y, z) carries 2^split_exp3(x, y, z)
-  uint32_t key = 0;
+  float G[5][5][5];  // the 125 values of the split (split_box32)
+  float E = 0.f;
   uint32_t bits = 0;
   if (act) {
     const float* qc = S.q32coef[in];
@@ -174,56 +206,16 @@ __device__ __forceinline__ void refine_box32(const Batch& p, int level, bool act
 #pragma unroll
     for (int t = 0; t < 27; ++t) A[t] = ldcg(qc + static_cast<uint64_t>(t) * S.q32cap + idx);
     const float m0 = ldcg(S.s32_m0 + slot);
-    const float E = fmaf(static_cast<float>(child_level) * 0x1p-20f, m0, ldcg(S.s32_e0 + slot));
-    key = fbits(E);
+    E = fmaf(static_cast<float>(child_level) * 0x1p-20f, m0, ldcg(S.s32_e0 + slot));
     if (!split_range_ok(m0)) bits = kStAmbig;  // redone in FP64
-    float P1[5][3][3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        float q[5];
-        split5uf(A[tix(0, j, k)], A[tix(1, j, k)], A[tix(2, j, k)], q);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) P1[i][j][k] = q[i];
-      }
-    float P2[5][5][3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        float q[5];
-        split5uf(P1[i][0][k], P1[i][1][k], P1[i][2][k], q);
-#pragma unroll
-        for (int j = 0; j < 5; ++j) P2[i][j][k] = q[j];
-      }
-#pragma unroll
-    for (int j = 0; j < 5; ++j)
-#pragma unroll
-      for (int i = 0; i < 5; ++i) split5uf(P2[i][j][0], P2[i][j][1], P2[i][j][2], G[i][j]);
+    split_box32(A, G);
   }
   uint32_t queue = 0;
   if (act && !bits) {
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
-      const int sx = 2 * (o & 1), sy = 2 * ((o >> 1) & 1), sz = 2 * (o >> 2);
-      bool nonpos = false, amb = false, notcert = false, amb2 = false;
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            const Sign3 q = sign_f_split(G[sx + i][sy + j][sz + k],
-                                         key, split_exp3(sx + i, sy + j, sz + k));
-            if ((i != 1) && (j != 1) && (k != 1)) {
-              nonpos |= q.nonpos;
-              amb |= !(q.nonpos | q.pos);
-            } else {
-              notcert |= q.nonpos;
-              amb2 |= !(q.nonpos | q.pos);
-            }
-          }
+      const Child32 q = classify_child32(G, 2 * (o & 1), 2 * ((o >> 1) & 1), 2 * (o >> 2), E);
+      const bool nonpos = q.nonpos, amb = q.amb, notcert = q.notcert, amb2 = q.amb2;
       if (nonpos) {
         bits |= kStInvalid;
       } else if (amb) {
@@ -266,8 +258,7 @@ __device__ __forceinline__ void refine_box32(const Batch& p, int level, bool act
           for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int i = 0; i < 3; ++i)
-              dst[static_cast<uint64_t>(tix(i, j, k)) * S.q32cap + pos] =
-                  down2f(G[sx + i][sy + j][sz + k], split_exp3(sx + i, sy + j, sz + k));
+              dst[static_cast<uint64_t>(tix(i, j, k)) * S.q32cap + pos] = G[sx + i][sy + j][sz + k];
         S.q32slot[out][pos] = slot;
       } else {
         bits |= kStOverflow;
