@@ -120,14 +120,17 @@ def best_config(precision, kind, n, dev_inputs, cache=CACHE, retune=False, reps=
     best_ms, best = final[0]
     if precision == "fp32":
         # the double-float redo pays off only when many elements escalate,
-        # and the pass's own first refinement level when many elements are
-        # decided there, which depends on the data: each tried on the winner
-        for opt in (hv.OPT_DFREDO, hv.OPT_LEVEL1):
-            trial = dict(best, options=best["options"] | opt)
-            ms = time_config(trial, precision, kind, dev_inputs, reps=3 * reps, **caps)
-            results.append((ms, trial))
-            if ms < best_ms:
-                best_ms, best = ms, trial
+        # and the first-level kernel when many elements are decided there,
+        # which depends on the data: each tried on every leader (the leaders'
+        # bulk passes are often within noise of each other, their
+        # combinations with an option not)
+        for _, leader in final:
+            for opt in (hv.OPT_DFREDO, hv.OPT_LEVEL1):
+                trial = dict(leader, options=leader["options"] | opt)
+                ms = time_config(trial, precision, kind, dev_inputs, reps=3 * reps, **caps)
+                results.append((ms, trial))
+                if ms < best_ms:
+                    best_ms, best = ms, trial
     best = dict(best)
     for name, values in KNOBS[precision]:
         best.setdefault(name, values[0])

@@ -1,8 +1,9 @@
 """Host logic of the autotuner (tune.py) with the timing stubbed out: it
 times every candidate, re-times the three leaders with three times the
-repetitions and keeps the fastest, tries the double-float redo on the FP32
-winner only, then the placement knobs one at a time, and caches the choice
-per device, precision, input kind and size bucket."""
+repetitions and keeps the fastest, tries the double-float redo and the
+first-level kernel on each FP32 leader, then the placement knobs one at a
+time, and caches the choice per device, precision, input kind and size
+bucket."""
 import json
 
 import pytest
@@ -37,8 +38,8 @@ def test_fastest_leader_is_kept_and_cached(stub, tmp_path):
     assert best == dict(options=hv.OPT_PREFETCH, bulk_threads=128, **defaults)
     n_cand = len(tune.candidates("fp32"))
     n_knob = sum(len(v) - 1 for _, v in tune.KNOBS["fp32"])
-    # all, the three leaders again, the redo and first-level trials, the knob trials
-    assert len(calls) == n_cand + 3 + 2 + n_knob
+    # all, the three leaders again, the redo and first-level trials on each, the knob trials
+    assert len(calls) == n_cand + 3 + 3 * 2 + n_knob
     assert all(r == 60 for _, r in calls[n_cand:])
     assert calls[n_cand + 3][0] == {"options": hv.OPT_PREFETCH | hv.OPT_DFREDO, "bulk_threads": 128}
     assert calls[n_cand + 4][0] == {"options": hv.OPT_PREFETCH | hv.OPT_LEVEL1, "bulk_threads": 128}
@@ -47,6 +48,16 @@ def test_fastest_leader_is_kept_and_cached(stub, tmp_path):
     calls.clear()
     assert tune.best_config("fp32", "indexed", 1000, None, cache=cache) == best
     assert calls == []  # from the cache
+
+
+def test_option_on_a_later_leader_can_win(stub, tmp_path):
+    """The fastest bulk pass alone (packed pairs) is not the fastest with the
+    first-level kernel: the option is tried on every leader."""
+    calls, speed = stub
+    speed.update({(hv.OPT_PAIR32, 64): 0.40, (0, 64): 0.41, (0, 128): 0.42,
+                  (hv.OPT_PAIR32 | hv.OPT_LEVEL1, 64): 0.35, (hv.OPT_LEVEL1, 64): 0.30})
+    best = tune.best_config("fp32", "soa", 10, None, cache=str(tmp_path / "c.json"))
+    assert (best["options"], best["bulk_threads"]) == (hv.OPT_LEVEL1, 64)
 
 
 def test_redo_kept_when_faster_and_never_for_fp64(stub, tmp_path):
