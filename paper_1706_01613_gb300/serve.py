@@ -19,6 +19,7 @@ The scheduling logic (`Scheduler`) is plain host code and is tested on the
 CPU with a fake executor; `GpuExecutor` runs the work through the C ABI.
 """
 import collections
+import gc
 import heapq
 import math
 import time
@@ -137,26 +138,34 @@ def run_stream(requests, executor, slots, budget_bytes, now=time.perf_counter, i
     sched = Scheduler(slots, budget_bytes, getattr(executor, "fixed_bytes", 0), small_slots,
                       small_n)
     order = sorted(requests, key=lambda r: r.arrival)
-    t0 = now()
-    executor.start()
-    nxt = 0
-    inflight = {}
-    while nxt < len(order) or sched.pending or inflight:
-        t = now() - t0
-        while nxt < len(order) and order[nxt].arrival <= t:
-            sched.arrive(order[nxt])
-            nxt += 1
-        for slot, req in sched.admissible():
-            req.admitted = t
-            executor.submit(slot, req)
-            inflight[slot] = req
-        for slot in list(inflight):
-            if executor.poll(slot):
-                req = inflight.pop(slot)
-                req.done = executor.finish(slot, req)
-                sched.release(slot, req)
-        if idle is not None:
-            idle()
+    # the loop's latency is the requests' latency: no pauses of the cyclic
+    # garbage collector while it runs (reference counting still frees)
+    gc_was_enabled = gc.isenabled()
+    gc.disable()
+    try:
+        t0 = now()
+        executor.start()
+        nxt = 0
+        inflight = {}
+        while nxt < len(order) or sched.pending or inflight:
+            t = now() - t0
+            while nxt < len(order) and order[nxt].arrival <= t:
+                sched.arrive(order[nxt])
+                nxt += 1
+            for slot, req in sched.admissible():
+                req.admitted = t
+                executor.submit(slot, req)
+                inflight[slot] = req
+            for slot in list(inflight):
+                if executor.poll(slot):
+                    req = inflight.pop(slot)
+                    req.done = executor.finish(slot, req)
+                    sched.release(slot, req)
+            if idle is not None:
+                idle()
+    finally:
+        if gc_was_enabled:
+            gc.enable()
     return sched
 
 
