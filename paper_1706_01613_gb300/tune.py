@@ -132,6 +132,7 @@ def best_config(precision, kind, n, dev_inputs, cache=CACHE, retune=False, reps=
     final = sorted(((time_config(c, precision, kind, dev_inputs, reps=3 * reps, **caps), c)
                     for _, c in results[:3]), key=lambda r: r[0])
     best_ms, best = final[0]
+    stage = list(final)  # the leaders and their option trials, under the default knobs
     if precision == "fp32":
         # the double-float redo pays off only when many elements escalate,
         # and the first-level kernel when many elements are decided there,
@@ -143,6 +144,7 @@ def best_config(precision, kind, n, dev_inputs, cache=CACHE, retune=False, reps=
                 trial = dict(leader, options=leader["options"] | opt)
                 ms = time_config(trial, precision, kind, dev_inputs, reps=3 * reps, **caps)
                 results.append((ms, trial))
+                stage.append((ms, trial))
                 if ms < best_ms:
                     best_ms, best = ms, trial
     best = dict(best)
@@ -154,6 +156,19 @@ def best_config(precision, kind, n, dev_inputs, cache=CACHE, retune=False, reps=
             results.append((ms, trial))
             if ms < best_ms:
                 best_ms, best = ms, trial
+    # the bulk pass and the options were chosen under the default knobs: the
+    # next best combinations of that stage again, with the knobs found
+    knobs = {name: best[name] for name, _ in KNOBS[precision]}
+    seen = [(best["options"], best["bulk_threads"])]
+    for _, c in sorted(stage, key=lambda r: r[0]):
+        if (c["options"], c["bulk_threads"]) in seen or len(seen) > 3:
+            continue
+        seen.append((c["options"], c["bulk_threads"]))
+        trial = dict(options=c["options"], bulk_threads=c["bulk_threads"], **knobs)
+        ms = time_config(trial, precision, kind, dev_inputs, reps=3 * reps, **caps)
+        results.append((ms, trial))
+        if ms < best_ms:
+            best_ms, best = ms, trial
     data[key] = {"config": best, "ms": best_ms,
                  "all": [{"config": c, "ms": m} for m, c in results],
                  "final": [{"config": c, "ms": m} for m, c in final]}

@@ -38,8 +38,9 @@ def test_fastest_leader_is_kept_and_cached(stub, tmp_path):
     assert best == dict(options=hv.OPT_PREFETCH, bulk_threads=128, **defaults)
     n_cand = len(tune.candidates("fp32"))
     n_knob = sum(len(v) - 1 for _, v in tune.KNOBS["fp32"])
-    # all, the three leaders again, the redo and first-level trials on each, the knob trials
-    assert len(calls) == n_cand + 3 + 3 * 2 + n_knob
+    # all, the three leaders again, the redo and first-level trials on each, the knob
+    # trials, the three next combinations again with the knobs found
+    assert len(calls) == n_cand + 3 + 3 * 2 + n_knob + 3
     assert all(r == 60 for _, r in calls[n_cand:])
     assert calls[n_cand + 3][0] == {"options": hv.OPT_PREFETCH | hv.OPT_DFREDO, "bulk_threads": 128}
     assert calls[n_cand + 4][0] == {"options": hv.OPT_PREFETCH | hv.OPT_LEVEL1, "bulk_threads": 128}
@@ -58,6 +59,28 @@ def test_option_on_a_later_leader_can_win(stub, tmp_path):
                   (hv.OPT_PAIR32 | hv.OPT_LEVEL1, 64): 0.35, (hv.OPT_LEVEL1, 64): 0.30})
     best = tune.best_config("fp32", "soa", 10, None, cache=str(tmp_path / "c.json"))
     assert (best["options"], best["bulk_threads"]) == (hv.OPT_LEVEL1, 64)
+
+
+def test_options_rechecked_with_the_knobs_found(stub, tmp_path):
+    """A combination that loses under the default knobs but wins with the
+    knobs found is taken."""
+    calls, speed = stub
+    speed.update({(hv.OPT_PAIR32 | hv.OPT_LEVEL1, 64): 0.30, (hv.OPT_LEVEL1, 64): 0.31,
+                  (hv.OPT_PAIR32, 64): 0.40, (0, 64): 0.41,
+                  ("esc_in_pass", 0): -0.05})
+    real = tune.time_config
+
+    def with_interaction(cfg, *a, **k):
+        ms = real(cfg, *a, **k)
+        if cfg.get("esc_in_pass") == 0 and cfg["options"] == hv.OPT_LEVEL1:
+            ms -= 0.05  # this combination gains more from the knob
+        return ms
+    tune.time_config = with_interaction
+    try:
+        best = tune.best_config("fp32", "soa", 10, None, cache=str(tmp_path / "d.json"))
+    finally:
+        tune.time_config = real
+    assert (best["options"], best["esc_in_pass"]) == (hv.OPT_LEVEL1, 0)
 
 
 def test_redo_kept_when_faster_and_never_for_fp64(stub, tmp_path):
