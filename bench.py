@@ -829,16 +829,20 @@ def main():
         rate, sample = oracle_rate(w, args.cpu_seconds, thr)
         cpu = {"value": rate, "unit": UNIT, "cores": thr, "kind": "oracle", "sample": sample}
 
-    quads = quad_run(max(5, args.steps // 20), 3, flush) if args.quads else None
-    filt = filter_run(max(5, args.steps // 50), 3, flush) if args.quads else None
-    mj = minj_run(w, dev_in, 5, 2, flush) if args.quads else None
-    qual = quality_run(w, dev_in, max(5, args.steps // 50), 3, flush) if args.quads else None
+    # the single-GPU sections (the other rows of the scope table, the other
+    # configurations, serving) only in a one-GPU run: with several ranks the
+    # others have left and their GPUs would be held for nothing
+    extras = args.quads and world == 1
+    quads = quad_run(max(5, args.steps // 20), 3, flush) if extras else None
+    filt = filter_run(max(5, args.steps // 50), 3, flush) if extras else None
+    mj = minj_run(w, dev_in, 5, 2, flush) if extras else None
+    qual = quality_run(w, dev_in, max(5, args.steps // 50), 3, flush) if extras else None
 
     # the other configurations (device-resident, both forms) and the serving
     # stream of the scope table: 10,000 requests, sizes log-uniform in
     # [100, 10^7], Poisson arrivals, both forms
     others, latency = {}, None
-    if args.configs and args.config == 2:
+    if args.configs and args.config == 2 and world == 1:
         v32.close()
         v64.close()
         del dev_in
