@@ -25,9 +25,10 @@
 // Refinement.  Level d holds boxes of depth d whose corners are certainly
 // positive and which are certainly not certified.  Each is split at 1/2
 // along xi, eta and zeta (quadratic de Casteljau: a row (p0, p1, p2) becomes
-// (p0, (p0+p1)/2, (p0+2p1+p2)/4, (p1+p2)/2, p2); the left child keeps the
-// first three, the right child the last three) and its 8 children of depth
-// d+1 are classified:
+// (p0, (p0+p1)/2, (p0+2p1+p2)/4, (p1+p2)/2, p2), computed unscaled with its
+// power-of-two factors kept apart as hexval_internal.cuh describes; the left
+// child keeps the first three, the right child the last three) and its 8
+// children of depth d+1 are classified:
 //   a corner coefficient certainly <= 0          -> element INVALID at d+1
 //   all 27 certainly > 0                         -> child certified
 //   corners certainly > 0, another certainly <=0 -> child queued for d+2
