@@ -120,6 +120,18 @@ typedef struct {
  *                      settle, go on to the tail's refinement.  Pays when
  *                      many elements are decided on level 1 (boundary
  *                      layers);
+ *  HEXVAL_OPT_PARTIAL64  FP32 form: each escalation the FP32 pass lists is
+ *                      first redone in part, one per thread in a kernel of
+ *                      its own: its FP32 classification is recomputed, and
+ *                      only the samples and edge coefficients FP32 left
+ *                      unsettled are evaluated in FP64, with the full
+ *                      evaluation's bound; a sample certainly <= 0 makes the
+ *                      element INVALID, everything certainly positive VALID
+ *                      (bmin / bmax then FP32), and whatever this cannot
+ *                      decide is redone in full by the tail.  Pays when
+ *                      escalations turn on few signs (near-degenerate
+ *                      corners); same verdicts.  Not with HEXVAL_OPT_DFREDO
+ *                      (hexval_create returns HEXVAL_E_ARG);
  *  HEXVAL_OPT_DFREDO   FP32 form: the escalations the FP32 pass leaves are
  *                      first redone in double-float (pairs of FP32 values,
  *                      about 44 bits, at FP32 throughput) by a kernel of its
@@ -142,7 +154,8 @@ enum {
   HEXVAL_OPT_PREFETCH = 2,
   HEXVAL_OPT_DFREDO = 4,
   HEXVAL_OPT_NO_REPLAY = 8,
-  HEXVAL_OPT_LEVEL1 = 16
+  HEXVAL_OPT_LEVEL1 = 16,
+  HEXVAL_OPT_PARTIAL64 = 32
 };
 
 typedef struct {
@@ -162,6 +175,8 @@ typedef struct {
   uint64_t boxes_fp32;      /* of boxes: split by the FP32 refinement */
   uint64_t redone_tail;     /* elements redone in FP64 by the tail kernel
                                (escalations the FP32 pass left) */
+  uint64_t partial_fp64;    /* of escalated_fp64: decided by the partial
+                               FP64 redo (HEXVAL_OPT_PARTIAL64) */
 } hexval_stats;
 
 /* Fills *cfg with the defaults listed above. */
@@ -343,6 +358,7 @@ enum {
   HEXVAL_PH_EXACT = 4,   /* unused: the exact tier runs inside the tail */
   HEXVAL_PH_REDODF = 5,  /* double-float redo of escalations (HEXVAL_OPT_DFREDO) */
   HEXVAL_PH_LEVEL1 = 6,  /* first refinement level in its own kernel (HEXVAL_OPT_LEVEL1) */
+  HEXVAL_PH_PARTIAL = 7, /* partial FP64 redo of escalations (HEXVAL_OPT_PARTIAL64) */
   HEXVAL_PH_COUNT = 8
 };
 typedef struct {

@@ -5,6 +5,8 @@
 //   [FP32 form, indexed]  nodes32 (once per call)
 //   bulk32 (FP32 form) or bulk64 (FP64 form) over all elements of the batch
 //   [FP32 form, HEXVAL_OPT_DFREDO]  redo_df: double-float redo of escalations
+//   [FP32 form, HEXVAL_OPT_PARTIAL64]  redo_partial: FP64 redo of only the
+//          signs FP32 left unsettled in each escalation
 //   [FP32 form, HEXVAL_OPT_LEVEL1]  level1: first refinement level of the
 //          elements listed for the FP32 refinement
 //   tail:  one cooperative launch that redoes the FP32 escalations in FP64,
@@ -132,6 +134,7 @@ const char* phase_name(int ph) {
     case HEXVAL_PH_TAIL: return "hexval tail";
     case HEXVAL_PH_REDODF: return "hexval redo_df";
     case HEXVAL_PH_LEVEL1: return "hexval level1";
+    case HEXVAL_PH_PARTIAL: return "hexval redo_partial";
     default: return "hexval";
   }
 }
@@ -164,6 +167,8 @@ int run_batches(hexval_ctx* h, Batch p, int64_t n_hex, cudaStream_t st) {
                          : phase(h, HEXVAL_PH_BULK64, st, [&] { return hexval::launch_bulk64(p, st); });
     if (e == cudaSuccess && fp32 && p.dfredo)
       e = phase(h, HEXVAL_PH_REDODF, st, [&] { return hexval::launch_redo_df(p, st); });
+    if (e == cudaSuccess && fp32 && p.partial64)
+      e = phase(h, HEXVAL_PH_PARTIAL, st, [&] { return hexval::launch_redo_partial(p, st); });
     if (e == cudaSuccess && fp32 && p.level1)
       e = phase(h, HEXVAL_PH_LEVEL1, st, [&] { return hexval::launch_level1(p, st); });
     if (e == cudaSuccess)
@@ -262,6 +267,7 @@ Batch indexed_batch(const hexval_ctx* h, int64_t n_nodes, const double* nodes,
   p.prefetch32 = (h->cfg.options & HEXVAL_OPT_PREFETCH) != 0;
   p.dfredo = (h->cfg.options & HEXVAL_OPT_DFREDO) != 0;
   p.level1 = (h->cfg.options & HEXVAL_OPT_LEVEL1) != 0;
+  p.partial64 = (h->cfg.options & HEXVAL_OPT_PARTIAL64) != 0;
   p.bulk_threads = static_cast<int>(h->cfg.bulk_threads);
   p.esc_in_pass = h->cfg.esc_in_pass;
   p.r32_in_pass = h->cfg.refine_in_pass;
@@ -303,7 +309,9 @@ int hexval_create(const hexval_config* cfg, hexval_handle* out) {
       cfg->queue_capacity > (1ull << 31) || cfg->exact_capacity == 0 ||
       cfg->exact_capacity > (1ull << 31) || cfg->max_nodes > (1ull << 31) ||
       (cfg->options & ~static_cast<uint32_t>(HEXVAL_OPT_PAIR32 | HEXVAL_OPT_PREFETCH | HEXVAL_OPT_DFREDO |
-                                             HEXVAL_OPT_NO_REPLAY | HEXVAL_OPT_LEVEL1)) ||
+                                             HEXVAL_OPT_NO_REPLAY | HEXVAL_OPT_LEVEL1 |
+                                             HEXVAL_OPT_PARTIAL64)) ||
+      ((cfg->options & HEXVAL_OPT_DFREDO) && (cfg->options & HEXVAL_OPT_PARTIAL64)) ||
       cfg->reserved || cfg->reserved2 || cfg->tail_warp_items < 1 || cfg->tail_warp_items > 64 ||
       (cfg->bulk_threads != 0 && cfg->bulk_threads != 64 && cfg->bulk_threads != 128 &&
        cfg->bulk_threads != 256))
@@ -392,6 +400,7 @@ int hexval_check_soa(hexval_handle h, int64_t n_hex, const double* corners, uint
   p.pair32 = (h->cfg.options & HEXVAL_OPT_PAIR32) != 0;
   p.dfredo = (h->cfg.options & HEXVAL_OPT_DFREDO) != 0;
   p.level1 = (h->cfg.options & HEXVAL_OPT_LEVEL1) != 0;
+  p.partial64 = (h->cfg.options & HEXVAL_OPT_PARTIAL64) != 0;
   p.bulk_threads = static_cast<int>(h->cfg.bulk_threads);
   p.esc_in_pass = h->cfg.esc_in_pass;
   p.r32_in_pass = h->cfg.refine_in_pass;
@@ -637,6 +646,7 @@ int hexval_get_stats(hexval_handle h, hexval_stats* out, int reset, void* stream
   out->escalated_df = s.escalated_df;
   out->boxes_fp32 = s.boxes_fp32;
   out->redone_tail = s.redone_tail;
+  out->partial_fp64 = s.partial_fp64;
   if (reset && cudaMemset(h->s.stats, 0, sizeof(s)) != cudaSuccess) return HEXVAL_E_CUDA;
   return HEXVAL_OK;
 }

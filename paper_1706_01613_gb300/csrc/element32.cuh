@@ -168,6 +168,32 @@ __device__ __forceinline__ int fp32_classify(const Scaled<float>& s, float E, fl
   return invalid ? 0 : (certified ? 1 : (refine ? 2 : 3));
 }
 
+// What FP32 leaves unsettled in an element it escalates (fp32_classify
+// outcome 3), for the FP64 redo of just those signs (fp64_partial,
+// element64.cuh): bits 0-7 the corner samples, 8-19 the edge samples, 20-31
+// the edge coefficients that are not certainly positive (the samples of an
+// escalated element are never certainly <= 0); bit 32: a face or the centre
+// not certainly positive, or an edge coefficient certainly <= 0.
+__device__ __forceinline__ uint64_t fp32_unsettled(const Scaled<float>& s, float E) {
+  uint64_t m = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (!(s.corner[k] > E)) m |= 1ull << k;
+#pragma unroll
+  for (int e = 0; e < 12; ++e)
+    if (!(s.edgeC[e] > 4.f * E)) m |= 1ull << (8 + e);
+  bool other = false;
+#pragma unroll
+  for (int e = 0; e < 12; ++e) {
+    if (s.edge[e] <= -2.f * E) other = true;
+    else if (!(s.edge[e] > 2.f * E)) m |= 1ull << (20 + e);
+  }
+#pragma unroll
+  for (int f = 0; f < 6; ++f) other |= !(s.face[f] > 4.f * E);
+  other |= !(s.centre > 8.f * E);
+  return other ? m | (1ull << 32) : m;
+}
+
 // The FP32 decision of one element (outcomes as fp32_classify).
 template <bool INDEXED>
 __device__ __forceinline__ int fp32_decide(const V3<float> Y[8], float X, bool bad, float& lo,

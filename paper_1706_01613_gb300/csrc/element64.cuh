@@ -196,4 +196,81 @@ __device__ __forceinline__ void fp64_element(const Batch& p, bool act, uint32_t 
   if (p.bmax) p.bmax[g] = hi;
 }
 
+// ------------------------------------------ redo of the unsettled signs ----
+// FP64 sample q of an element from its edge vectors (q < 8: corner node q;
+// otherwise the sample of edge q - 8, C = 4 J at its midpoint), with the
+// operations coefficients_from_edges uses for it, so within its FP64 bound.
+static __device__ __noinline__ double sample64(const V3<double>* a, const V3<double>* b,
+                                               const V3<double>* g, int q) {
+  switch (q) {
+    case 0: return det3(a[0], b[0], g[0]);
+    case 1: return det3(a[0], b[1], g[1]);
+    case 2: return det3(a[1], b[1], g[3]);
+    case 3: return det3(a[1], b[0], g[2]);
+    case 4: return det3(a[2], b[2], g[0]);
+    case 5: return det3(a[2], b[3], g[1]);
+    case 6: return det3(a[3], b[3], g[3]);
+    case 7: return det3(a[3], b[2], g[2]);
+    case 8: return det3(a[0], vadd(b[0], b[1]), vadd(g[0], g[1]));
+    case 9: return det3(a[1], vadd(b[0], b[1]), vadd(g[2], g[3]));
+    case 10: return det3(a[2], vadd(b[2], b[3]), vadd(g[0], g[1]));
+    case 11: return det3(a[3], vadd(b[2], b[3]), vadd(g[2], g[3]));
+    case 12: return det3(vadd(a[0], a[1]), b[0], vadd(g[0], g[2]));
+    case 13: return det3(vadd(a[0], a[1]), b[1], vadd(g[1], g[3]));
+    case 14: return det3(vadd(a[2], a[3]), b[2], vadd(g[0], g[2]));
+    case 15: return det3(vadd(a[2], a[3]), b[3], vadd(g[1], g[3]));
+    case 16: return det3(vadd(a[0], a[2]), vadd(b[0], b[2]), g[0]);
+    case 17: return det3(vadd(a[0], a[2]), vadd(b[1], b[3]), g[1]);
+    case 18: return det3(vadd(a[1], a[3]), vadd(b[0], b[2]), g[2]);
+    case 19: return det3(vadd(a[1], a[3]), vadd(b[1], b[3]), g[3]);
+    default: return 0.0;
+  }
+}
+
+// FP64 edge coefficient e (scaled by 2, as Scaled::edge): the edge sample
+// less the corner samples of the edge's two end nodes, as
+// coefficients_from_edges forms it.
+static __device__ __noinline__ double edge64(const V3<double>* a, const V3<double>* b,
+                                             const V3<double>* g, int e) {
+  int ca, cb;
+  if (e < 4) {  // xi-edge at (eta, zeta) = (e & 1, e >> 1)
+    ca = node_at(0, e & 1, e >> 1);
+    cb = node_at(1, e & 1, e >> 1);
+  } else if (e < 8) {  // eta-edge at (xi, zeta)
+    ca = node_at((e - 4) & 1, 0, (e - 4) >> 1);
+    cb = node_at((e - 4) & 1, 1, (e - 4) >> 1);
+  } else {  // zeta-edge at (xi, eta)
+    ca = node_at((e - 8) & 1, (e - 8) >> 1, 0);
+    cb = node_at((e - 8) & 1, (e - 8) >> 1, 1);
+  }
+  return sample64(a, b, g, 8 + e) - sample64(a, b, g, ca) - sample64(a, b, g, cb);
+}
+
+// Depth-0 decision of an element the FP32 pass escalated, redoing in FP64
+// only the signs FP32 left unsettled (mask: fp32_unsettled), each with the
+// bound of the full FP64 evaluation (fp64_element: the same E from the same
+// FP64 edge vectors).  A redone sample certainly <= 0 makes the element
+// INVALID (Sec. 6, Step 2); all samples and all 27 coefficients certainly
+// positive -- those FP32 certified and those redone -- make it VALID (Step 4).
+// X: the element's nodes.  Returns 0 (INVALID@0), 1 (VALID@0), or -1 when
+// the full FP64 evaluation is needed (a sign still unsettled, a face or
+// centre coefficient, a coefficient certainly <= 0, non-finite coordinates).
+__device__ __forceinline__ int fp64_partial(const V3<double> X[8], uint64_t mask) {
+  if (nonfinite_d(X)) return -1;
+  V3<double> a[4], b[4], gg[4];
+  edges_from_nodes(X, a, b, gg);
+  const Keys K = keys_d(pow2d(min(3 * max_exponent_d(a, b, gg) - 3107, 1000)));
+  bool open = false;
+  for (uint32_t m = static_cast<uint32_t>(mask) & 0xfffffu; m; m &= m - 1) {
+    const int q = __ffs(m) - 1;
+    const Sign3 c = sign_d(sample64(a, b, gg, q), q < 8 ? K.k1 : K.k4);
+    if (c.nonpos) return 0;
+    open |= !c.pos;
+  }
+  if (open || (mask >> 32)) return -1;
+  for (uint32_t m = static_cast<uint32_t>(mask >> 20) & 0xfffu; m; m &= m - 1)
+    if (!sign_d(edge64(a, b, gg, __ffs(m) - 1), K.k2).pos) return -1;
+  return 1;
+}
+
 }  // namespace hexval

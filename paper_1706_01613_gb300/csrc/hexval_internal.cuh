@@ -68,13 +68,14 @@ struct Counters {
   unsigned int minj_next;                   // element counter of the minimum-of-J kernel
   unsigned int iw_count;                    // in-warp refinement workspaces taken
   unsigned int iw_done;                     // elements decided by the in-warp refinement
-  unsigned int esc3_count;                  // double-float redo -> tail (list esc3)
+  unsigned int esc3_count;                  // double-float or partial FP64 redo -> tail (esc3)
   unsigned int df_count;                    // decided by the double-float redo
   unsigned int xb_count;                    // exact-check list (boxes)
   unsigned int l1_count;                    // elements the first-level kernel split
   unsigned int r32b_count;                  // of those, left undecided (list r32b)
   unsigned int split64;                     // FP64 boxes split by the refinement
   unsigned int split32;                     // FP32 boxes split by the refinement
+  unsigned int part_count;                  // escalations the partial FP64 redo decided
 };
 
 // Escalations of the FP32 pass: the first Batch::esc_in_pass elements
@@ -99,7 +100,7 @@ constexpr unsigned int kIwBoxes = 64;
 // Counters accumulated across calls (hexval_get_stats).
 struct Stats {
   unsigned long long elements, escalated_fp64, refined, boxes, exact, max_level_boxes,
-      escalated_df, boxes_fp32, redone_tail;
+      escalated_df, boxes_fp32, redone_tail, partial_fp64;
 };
 
 // Device scratch owned by a handle.
@@ -154,7 +155,8 @@ struct Scratch {
   float* s32_m0;
   // FP32 form: workspaces of the in-warp FP64 refinement (warp_items.cuh)
   double* iw;
-  // FP32 form: elements the double-float redo leaves to FP64 (redo_df.cu)
+  // FP32 form: elements the double-float redo (redo_df.cu) or the partial
+  // FP64 redo (redo_partial.cu) leaves to the full FP64 redo
   uint32_t* esc3;
   // FP32 form: elements the first-level kernel leaves to the tail (level1.cu)
   uint32_t* r32b;
@@ -176,6 +178,7 @@ struct Batch {
   int prefetch32;    // indexed FP32 pass on a persistent grid with prefetch
   int dfredo;        // FP32 form: escalations redone in double-float first
   int level1;        // FP32 form: first refinement level in a kernel of its own
+  int partial64;     // FP32 form: escalations first redone only in their unsettled signs
   unsigned int esc_in_pass;  // FP32 escalations of a batch redone in FP64 by the FP32 pass
   unsigned int r32_in_pass;  // elements to refine redone in FP64 by the FP32 pass
   unsigned int warp_items;   // tail: warp-per-item steps up to this many items per warp
@@ -682,6 +685,9 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned int grid, unsig
 // FP32 form with HEXVAL_OPT_DFREDO: double-float redo of the escalations
 // the FP32 pass leaves (between the bulk and tail kernels).
 cudaError_t launch_redo_df(const Batch& p, cudaStream_t st);
+// FP32 form with HEXVAL_OPT_PARTIAL64: FP64 redo of the unsettled signs of
+// the escalations the FP32 pass leaves (between the bulk and tail kernels).
+cudaError_t launch_redo_partial(const Batch& p, cudaStream_t st);
 // FP32 form with HEXVAL_OPT_LEVEL1: the first refinement level of the
 // elements the FP32 pass lists for the FP32 refinement (before the tail).
 cudaError_t launch_level1(const Batch& p, cudaStream_t st);

@@ -3,8 +3,8 @@
 //           listed (refine32.cuh); elements whose signs FP32 cannot settle
 //           are listed for the FP64 redo;
 //  phase E  (FP32 form) the escalated elements the FP32 pass (or the
-//           double-float redo) left, and those of phase R, redone in FP64
-//           (element64.cuh);
+//           double-float or the partial FP64 redo) left, and those of
+//           phase R, redone in FP64 (element64.cuh);
 //  phase X0 elements whose root signs could not be certified: decided
 //           exactly at depth 0, or refined from their FP64 root box;
 //  levels   refinement of undecided elements (Sec. 6, recursive_subdivision),
@@ -449,6 +449,7 @@ __device__ __forceinline__ void fold_stats_and_reset(const Batch& p, unsigned in
       atomicAdd(&st->escalated_df, static_cast<unsigned long long>(ldcg(&C->df_count)));
       atomicMax(&st->max_level_boxes, mx);
       atomicAdd(&st->redone_tail, static_cast<unsigned long long>(n_redo));
+      atomicAdd(&st->partial_fp64, static_cast<unsigned long long>(ldcg(&C->part_count)));
     }
   }
   __syncthreads();  // every read above is done before the reset
@@ -463,11 +464,13 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
   const Scratch& S = p.s;
   Counters* C = S.cnt;
   // escalation list entries [esc_in_pass, n_list) are left for this kernel,
-  // or, after the double-float redo, the esc3 list it leaves
+  // or, after the double-float or the partial FP64 redo, the esc3 list it
+  // leaves
   const unsigned int n_list = from_list ? ldcg(&C->esc_count) : 0u;
   const unsigned int n_esc = !from_list ? 0u
-                             : p.dfredo ? ldcg(&C->esc3_count)
-                                        : (n_list > p.esc_in_pass ? n_list - p.esc_in_pass : 0u);
+                             : p.dfredo || p.partial64
+                                 ? ldcg(&C->esc3_count)
+                                 : (n_list > p.esc_in_pass ? n_list - p.esc_in_pass : 0u);
   // refinement list entries [r32_in_pass, n_rl) are left for this kernel,
   // or, after the first-level kernel, the r32b list it leaves
   const unsigned int n_rl = from_list ? ldcg(&C->r32_count) : 0u;
@@ -511,7 +514,7 @@ __global__ void __launch_bounds__(kTailThreads, 1) tail_kernel(Batch p, int from
     if (go) n_esc2 = ldcg(&C->esc2_count);
   }
   if (go && n_esc + n_esc2) {  // phase E: list entries, then the FP32 refinement's
-    const uint32_t* esc = p.dfredo ? S.esc3 : S.esc + p.esc_in_pass;
+    const uint32_t* esc = p.dfredo || p.partial64 ? S.esc3 : S.esc + p.esc_in_pass;
     const unsigned int n_e = n_esc + n_esc2;
     n_redo = n_e;
     if (n_e <= warp_items) {

@@ -25,6 +25,7 @@ OPT_PREFETCH = 2  # hexval_config.options: persistent indexed FP32 pass with pre
 OPT_DFREDO = 4    # hexval_config.options: double-float redo of FP32 escalations
 OPT_NO_REPLAY = 8 # hexval_config.options: no graph replay of repeated check calls
 OPT_LEVEL1 = 16   # hexval_config.options: first refinement level in a kernel of its own
+OPT_PARTIAL64 = 32  # hexval_config.options: the unsettled signs of escalations redone in FP64 first
 VALID, INVALID, UNDECIDED, NONFINITE = 1, 2, 3, 4
 
 # every function declared in include/hexval.h (the CPU test checks the list)
@@ -35,7 +36,7 @@ EXPORTS = ("hexval_config_default", "hexval_create", "hexval_destroy", "hexval_c
            "hexval_corner_quality_indexed", "hexval_compact", "hexval_min_jacobian",
            "hexval_min_jacobian_indexed", "hexval_strerror", "hexval_scratch_bytes",
            "hexval_copy_soa_range", "hexval_prepare_nodes", "hexval_check_indexed_prepared")
-PHASES = ("nodes32", "bulk32", "bulk64", "tail", "-", "redo_df", "level1", "-")
+PHASES = ("nodes32", "bulk32", "bulk64", "tail", "-", "redo_df", "level1", "redo_partial")
 
 
 class Config(ctypes.Structure):
@@ -52,7 +53,7 @@ class Config(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint64) for k in
                 ("elements", "escalated_fp64", "refined", "boxes", "exact", "max_level_boxes",
-                 "escalated_df", "boxes_fp32", "redone_tail")]
+                 "escalated_df", "boxes_fp32", "redone_tail", "partial_fp64")]
 
 
 class Profile(ctypes.Structure):
@@ -149,7 +150,7 @@ class Validator:
     of the default configuration (max_depth, queue_capacity, max_batch,
     max_nodes, exact_capacity, bulk_threads, esc_in_pass, refine_in_pass,
     tail_warp_items, options = OPT_* bits: PAIR32, PREFETCH, DFREDO,
-    NO_REPLAY, LEVEL1).  Repeated identical check calls are
+    NO_REPLAY, LEVEL1, PARTIAL64).  Repeated identical check calls are
     replayed from a CUDA graph unless NO_REPLAY is set."""
 
     def __init__(self, precision="fp64", max_depth=8, device=None, **caps):

@@ -134,13 +134,14 @@ def best_config(precision, kind, n, dev_inputs, cache=CACHE, retune=False, reps=
     best_ms, best = final[0]
     stage = list(final)  # the leaders and their option trials, under the default knobs
     if precision == "fp32":
-        # the double-float redo pays off only when many elements escalate,
+        # the double-float and partial FP64 redos pay off only when many
+        # elements escalate (the partial one when they turn on few signs),
         # and the first-level kernel when many elements are decided there,
         # which depends on the data: each tried on every leader (the leaders'
         # bulk passes are often within noise of each other, their
         # combinations with an option not)
         for _, leader in final:
-            for opt in (hv.OPT_DFREDO, hv.OPT_LEVEL1):
+            for opt in (hv.OPT_DFREDO, hv.OPT_LEVEL1, hv.OPT_PARTIAL64):
                 trial = dict(leader, options=leader["options"] | opt)
                 ms = time_config(trial, precision, kind, dev_inputs, reps=3 * reps, **caps)
                 results.append((ms, trial))

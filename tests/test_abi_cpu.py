@@ -87,9 +87,11 @@ def test_binding_constants_match_the_header():
     assert vals["HEXVAL_OPT_DFREDO"] == hv.OPT_DFREDO
     assert vals["HEXVAL_OPT_NO_REPLAY"] == hv.OPT_NO_REPLAY
     assert vals["HEXVAL_OPT_LEVEL1"] == hv.OPT_LEVEL1
+    assert vals["HEXVAL_OPT_PARTIAL64"] == hv.OPT_PARTIAL64
     assert len(hv.PHASES) == vals["HEXVAL_PH_COUNT"]
     for name, ph in (("nodes32", "NODES32"), ("bulk32", "BULK32"), ("bulk64", "BULK64"),
-                     ("tail", "TAIL"), ("redo_df", "REDODF"), ("level1", "LEVEL1")):
+                     ("tail", "TAIL"), ("redo_df", "REDODF"), ("level1", "LEVEL1"),
+                     ("redo_partial", "PARTIAL")):
         assert hv.PHASES.index(name) == vals["HEXVAL_PH_" + ph]
     body = re.search(r"typedef struct \{([^}]*)\} hexval_stats;", _header()).group(1)
     fields = re.findall(r"uint64_t\s+(\w+);", body)
@@ -100,7 +102,10 @@ def test_binding_constants_match_the_header():
 
 def test_options_outside_the_known_bits_are_refused(lib):
     bad = hv.default_config()
-    bad.options = 32
+    bad.options = 64
+    assert lib.hexval_create(ctypes.byref(bad), ctypes.byref(ctypes.c_void_p())) == -1
+    bad = hv.default_config()  # two redos of the same escalation list
+    bad.options = hv.OPT_DFREDO | hv.OPT_PARTIAL64
     assert lib.hexval_create(ctypes.byref(bad), ctypes.byref(ctypes.c_void_p())) == -1
     bad = hv.default_config()
     bad.reserved = 1

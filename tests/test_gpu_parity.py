@@ -309,6 +309,55 @@ def test_double_float_redo_of_many_escalations(kind):
     assert runs[1][1]["escalated_df"] == 0
 
 
+@pytest.mark.parametrize("kind", ["soa", "indexed"])
+def test_partial_fp64_redo_of_escalations(kind):
+    """HEXVAL_OPT_PARTIAL64, no escalation redone inside the FP32 pass
+    (esc_in_pass 0): the partial redo evaluates in FP64 only the samples
+    and edge coefficients FP32 left unsettled, the tail redoes the rest.  About 25,000 near-degenerate
+    elements in 500,000 (one corner moved: few signs open) and twisted
+    boundary-layer prisms (refinement in the same batch), depth caps 0, 1
+    and 8: flags identical to the run without the option, exact against the
+    oracle on every near-degenerate element, every prism and a sample of the
+    others, and the statistics count the elements the partial redo decided."""
+    X, deg_kind, _ = synth.affine_mixture(500_000, seed=20170021)
+    T = synth.twisted_layers(20_000, seed=20170022, theta_max_deg=150.0)
+    X = np.ascontiguousarray(np.concatenate([X, T], axis=2))
+    deg_kind = np.concatenate([deg_kind, np.full(T.shape[2], 3, np.int8)])
+    n = X.shape[2]
+    nodes = np.ascontiguousarray(X.transpose(2, 0, 1).reshape(8 * n, 3))
+    conn = np.arange(8 * n, dtype=np.int32).reshape(n, 8)
+    for depth in (8, 1, 0):
+        runs = []
+        for opt in (hv.OPT_PARTIAL64, 0):
+            v = hv.Validator(precision="fp32", max_depth=depth, options=opt, esc_in_pass=0,
+                             **CAPS)
+            v.stats(reset=True)
+            if kind == "soa":
+                got = _run_soa(v, X)
+            else:
+                got = [t.cpu().numpy() for t in v.check_indexed(torch.from_numpy(nodes).cuda(),
+                                                                torch.from_numpy(conn).cuda())]
+                got.append(v.status())
+            runs.append((got, v.stats()))
+            v.close()
+        (f, lo, hi, rc), st = runs[0]
+        assert rc == 0 and runs[1][0][3] == 0
+        assert np.array_equal(f, runs[1][0][0])
+        print(kind, depth, st)
+        # the partial redo's leftovers are the tail's to redo in full
+        assert 0 < st["partial_fp64"]
+        assert st["partial_fp64"] + st["redone_tail"] <= st["escalated_fp64"]
+        assert runs[1][1]["partial_fp64"] == 0
+        if depth != 8:
+            continue
+        deg = np.nonzero(deg_kind == 1)[0]
+        rest = np.random.default_rng(6).choice(np.nonzero((deg_kind != 1) & (deg_kind != 3))[0],
+                                               20_000, replace=False)
+        for idx in (deg, rest, np.nonzero(deg_kind == 3)[0]):
+            Xi = np.ascontiguousarray(X[:, :, idx])
+            _compare("fp32", (f[idx], lo[idx], hi[idx]), oracle.check_soa(Xi, max_depth=8), Xi)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_repeated_calls_replay_a_graph(prec):
     """Identical calls are replayed from a graph the library captures on the
@@ -550,7 +599,7 @@ def test_autotuner_picks_a_candidate_and_stays_exact(tmp_path):
     dev = (torch.from_numpy(nodes).cuda(), torch.from_numpy(conn).cuda())
     cache = str(tmp_path / "tune.json")
     best = tune.best_config("fp32", "indexed", len(conn), dev, cache=cache, reps=3, **CAPS)
-    launch = {"options": best["options"] & ~(hv.OPT_DFREDO | hv.OPT_LEVEL1),
+    launch = {"options": best["options"] & ~(hv.OPT_DFREDO | hv.OPT_LEVEL1 | hv.OPT_PARTIAL64),
               "bulk_threads": best["bulk_threads"]}
     assert launch in tune.candidates("fp32")
     assert tune.best_config("fp32", "indexed", len(conn), dev, cache=cache, **CAPS) == best

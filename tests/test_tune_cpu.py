@@ -1,9 +1,9 @@
 """Host logic of the autotuner (tune.py) with the timing stubbed out: it
 times every candidate, re-times the three leaders with three times the
-repetitions and keeps the fastest, tries the double-float redo and the
-first-level kernel on each FP32 leader, then the placement knobs one at a
-time, and caches the choice per device, precision, input kind and size
-bucket."""
+repetitions and keeps the fastest, tries the double-float redo, the
+first-level kernel and the partial FP64 redo on each FP32 leader, then the
+placement knobs one at a time, and caches the choice per device, precision,
+input kind and size bucket."""
 import json
 
 import pytest
@@ -38,12 +38,14 @@ def test_fastest_leader_is_kept_and_cached(stub, tmp_path):
     assert best == dict(options=hv.OPT_PREFETCH, bulk_threads=128, **defaults)
     n_cand = len(tune.candidates("fp32"))
     n_knob = sum(len(v) - 1 for _, v in tune.KNOBS["fp32"])
-    # all, the three leaders again, the redo and first-level trials on each, the knob
+    # all, the three leaders again, the three option trials on each, the knob
     # trials, the three next combinations again with the knobs found
-    assert len(calls) == n_cand + 3 + 3 * 2 + n_knob + 3
+    assert len(calls) == n_cand + 3 + 3 * 3 + n_knob + 3
     assert all(r == 60 for _, r in calls[n_cand:])
     assert calls[n_cand + 3][0] == {"options": hv.OPT_PREFETCH | hv.OPT_DFREDO, "bulk_threads": 128}
     assert calls[n_cand + 4][0] == {"options": hv.OPT_PREFETCH | hv.OPT_LEVEL1, "bulk_threads": 128}
+    assert calls[n_cand + 5][0] == {"options": hv.OPT_PREFETCH | hv.OPT_PARTIAL64,
+                                    "bulk_threads": 128}
     data = json.load(open(cache))
     assert data["dev|fp32|indexed|1000"]["config"] == best
     calls.clear()
@@ -90,7 +92,7 @@ def test_redo_kept_when_faster_and_never_for_fp64(stub, tmp_path):
     assert best["options"] == hv.OPT_DFREDO and best["bulk_threads"] == 64
     calls.clear()
     best64 = tune.best_config("fp64", "soa", 10, None, cache=str(tmp_path / "b.json"))
-    assert all(not (c["options"] & hv.OPT_DFREDO) for c, _ in calls)
+    assert all(not (c["options"] & (hv.OPT_DFREDO | hv.OPT_PARTIAL64)) for c, _ in calls)
     assert best64["options"] == 0
 
 
