@@ -46,6 +46,10 @@ def test_fastest_leader_is_kept_and_cached(stub, tmp_path):
     assert calls[n_cand + 4][0] == {"options": hv.OPT_PREFETCH | hv.OPT_LEVEL1, "bulk_threads": 128}
     assert calls[n_cand + 5][0] == {"options": hv.OPT_PREFETCH | hv.OPT_PARTIAL64,
                                     "bulk_threads": 128}
+    # the two redos of the escalation list are never combined (hexval_create
+    # refuses that)
+    both = hv.OPT_DFREDO | hv.OPT_PARTIAL64
+    assert all(c["options"] & both != both for c, _ in calls)
     data = json.load(open(cache))
     assert data["dev|fp32|indexed|1000"]["config"] == best
     calls.clear()
