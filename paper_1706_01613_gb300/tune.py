@@ -2,16 +2,20 @@
 
 For a workload shape (precision, input kind, size) it times every candidate
 launch configuration of the handle (FP32 bulk pass scalar, staged or packed
-f32x2; bulk block size; for the FP64 form the block size), re-times the
-leaders, then tries on the winner the double-float redo of escalations and
-the FP32 pass's own first refinement level (FP32 form) and, one knob at a
-time, the placement of the uneven work: how
-many FP32 escalations and elements to refine the bulk pass keeps for itself
-(esc_in_pass, refine_in_pass) and the tail kernel's threshold between
-one item per warp and one per thread (tail_warp_items).  Timing is on a
-sample input through the C ABI, with CUDA events on the launch stream.  Results are cached per device name in
-a JSON file (default ~/.cache/hexval/tune.json, or $HEXVAL_TUNE_CACHE) so a
-shape is tuned once.
+f32x2; bulk block size; for the FP64 form the block size) and re-times the
+three leaders.  For the FP32 form it then tries on each leader, one at a
+time, the options that move work out of the tail: the double-float redo of
+the escalations, the partial FP64 redo of their unsettled signs, the first
+refinement level in a kernel of its own.  On the winner it tries, one knob at
+a time, the placement of the uneven work: how many FP32 escalations and
+elements to refine the bulk pass keeps for itself (esc_in_pass,
+refine_in_pass) and the tail kernel's threshold between one item per warp and
+one per thread (tail_warp_items); finally the next best pass / option
+combinations are timed again with the knobs found.  Timing is on a sample
+input through the C ABI, with CUDA events on the launch stream and the L2
+flushed before each call.  Results are cached per device name in a JSON file
+(default ~/.cache/hexval/tune.json, or $HEXVAL_TUNE_CACHE) so a shape is
+tuned once.
 
     cfg = tune.best_config("fp32", "indexed", n_hex, sample=(nodes, conn))
     v = hexval.Validator(precision="fp32", **cfg)
