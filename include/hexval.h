@@ -102,8 +102,9 @@ typedef struct {
   uint32_t reserved2;      /* must be 0 */
 } hexval_config;
 
-/* options (tuning knobs; the same flags, and with HEXVAL_OPT_DFREDO the
- * bounds of the elements it decides carry its error instead of FP64's):
+/* options (tuning knobs; the same flags, and with HEXVAL_OPT_DFREDO or
+ * HEXVAL_OPT_PARTIAL64 the bmin / bmax of the escalated elements they decide
+ * carry double-float or FP32 error instead of FP64's):
  *  HEXVAL_OPT_PAIR32   the FP32 bulk pass with two elements per thread in
  *                      packed f32x2 arithmetic instead of one per thread;
  *  HEXVAL_OPT_PREFETCH the indexed FP32 bulk pass on a persistent grid that
